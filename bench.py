@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the sputtered-atom transport hot path on GB300.
+
+A step transports the whole quaternary co-sputter workload (Ni/Pd/Pt/Ru,
+4 cathodes tilted 30 deg confocal at 120 mm, 1e7 particles each, Ar 0.5 Pa,
+300 K, 100 mm wafer with 200x200 int64 counts + fp64 energy per cathode)
+through libsput.so.  The metric is particle-collisions/s (and landed
+particles/s), whole job, inputs resident in HBM; ``e2e`` is the same metric
+through the host-buffer entry point with the host<->device copies inside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank transports its own replica of the workload
+(distinct seeds, no data-path collective: particles are independent) and the
+job value is the sum over ranks divided by the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle on bounded samples of the same
+workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-collisions/sec and landed particles/sec on 1 GB300 vs oracle; roofline fraction"
+UNIT = "collisions/s"
+WORKLOAD = ("quaternary co-sputter Ni/Pd/Pt/Ru, 4 cathodes tilted 30 deg confocal at 120 mm, "
+            "4 x 1e7 particles, Ar 0.5 Pa 300 K, E_i 400 eV, 100 mm wafer, 200x200 int64 counts + fp64 energy")
+# Lane-instructions the transport kernel executes per collision on this
+# workload, from one ncu capture (smsp__thread_inst_executed.sum divided by
+# the collisions of that launch); see profiles/transport_quaternary_ncu.md.
+LANE_OPS_PER_COLLISION = float(os.environ.get("SPUT_LANE_OPS_PER_COLLISION", "2300"))
+# dram bytes per launch of the full workload from the same capture (None until measured)
+TRAFFIC_PER_LAUNCH = None
+LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes issue one instruction per clock each
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (200 ms period)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception as e:  # no nvidia-smi: report nothing rather than guess
+            log("clock sampling unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        out["samples"] = len(rows)
+        out["sm_mhz"] = statistics.median(sm) if sm else None
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        out["sm_max_mhz"] = max(mx) if mx else None
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        out["power_w_max"] = max(pw) if pw else None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(nm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ------------------------------------------------------------- reference arm
+def cpu_oracle_rate(n_per_cathode, n_threads=None):
+    """Oracle collisions/s and landed/s on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    sc = workloads.scene_quaternary(n_per_cathode=n_per_cathode)
+    o = oracle.OracleScene(sc)
+    n_threads = n_threads or (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    out = o.run_all(n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    coll = int(out["ncoll"].sum())
+    landed = int(np.sum(out["prim"] >= 0))
+    return {"collisions": coll, "landed": landed, "seconds": dt, "cores": n_threads,
+            "particles": sc.total_particles}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n_per = args.ref_particles
+    for _ in range(args.warmup):
+        cpu_oracle_rate(max(1, n_per // 8))
+    tot_c = tot_l = tot_t = 0.0
+    cores = 0
+    for _ in range(args.steps):
+        r = cpu_oracle_rate(n_per)
+        tot_c += r["collisions"]
+        tot_l += r["landed"]
+        tot_t += r["seconds"]
+        cores = r["cores"]
+    value = tot_c / tot_t
+    sample = f"{4 * n_per} particles ({n_per} per cathode) of the workload per step, all host cores"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "landed_per_s": tot_l / tot_t,
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2411_14413_gb300 as pkg
+    import workloads
+    from paper_2411_14413_gb300 import _native as N
+    from paper_2411_14413_gb300 import api
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    # CPU baseline first (rank 0, N = 1 only), before the GPU work starts
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_oracle_rate(args.cpu_particles)
+        cpu = {"value": r["collisions"] / r["seconds"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r['particles']} particles ({args.cpu_particles} per cathode) of the workload, "
+                         f"{r['seconds']:.1f} s wall on {r['cores']} threads",
+               "landed_per_s": r["landed"] / r["seconds"]}
+        log("cpu baseline:", cpu)
+
+    sc = workloads.scene_quaternary(n_per_cathode=args.particles)
+    tr = pkg.Transport(sc, device=local_rank, energy=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+    seed0 = 1000 * rank
+
+    for w in range(args.warmup):
+        st = tr.run(seed=seed0 + 10_000 + w, want_stats=True)
+        log(f"warmup {w}: {st.collisions} collisions, kernel {st.kernel_ms:.2f} ms")
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.25)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    for k in range(args.steps):
+        flush.zero_()                                       # L2 flush, outside the timed events
+        ev[k][0].record(stream)
+        st = tr.run(seed=seed0 + k, stream=stream.cuda_stream, want_stats=True)
+        ev[k][1].record(stream)
+        stats.append(st.as_dict())
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    coll = sum(s["collisions"] for s in stats)
+    landed = sum(s["landed"] for s in stats)
+    kernel_ms = [s["kernel_ms"] for s in stats]
+
+    # e2e through the host-buffer entry point: instance table H2D + tallies D2H each step
+    L = tr.layout
+    pin = lambda shape, dt: torch.zeros(shape, dtype=dt, pin_memory=True)
+    host = {"counts": pin((L.n_instances, L.ny, L.nx), torch.int64),
+            "energy": pin((L.n_instances, L.ny, L.nx), torch.float64),
+            "prim_counts": pin((L.n_instances, L.max_prims), torch.int64),
+            "timed_out": pin((L.n_instances,), torch.int64)}
+    ht = N.sput_tallies()
+    for k2, v in host.items():
+        setattr(ht, k2, v.data_ptr())
+    d2h = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = len(sc.instances) * 40
+    e2e_coll = 0
+    e2e_t = 0.0
+    if not args.no_e2e:
+        api.sput_run_host(tr.h, api.run_opts(seed=seed0 + 777), ht)  # warm the staging buffers
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            api.sput_instances_set(tr.h, sc)
+            st = api.sput_run_host(tr.h, api.run_opts(seed=seed0 + 500 + k), ht)
+            e2e_coll += st.collisions
+        e2e_t = time.perf_counter() - t0
+
+    # max over ranks of the time, sum over ranks of the work
+    vec = torch.tensor([total_ms, coll, landed, e2e_t, e2e_coll], dtype=torch.float64, device=dev)
+    if dist is not None:
+        tmax = vec.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = vec.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms_all, e2e_t_all = tmax[0].item(), tmax[3].item()
+        coll_all, landed_all, e2e_coll_all = tsum[1].item(), tsum[2].item(), tsum[4].item()
+    else:
+        total_ms_all, e2e_t_all = total_ms, e2e_t
+        coll_all, landed_all, e2e_coll_all = coll, landed, e2e_coll
+    tr.close()
+    if rank != 0:
+        return
+
+    value = coll_all / (total_ms_all / 1e3)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * LANES_PER_SM_PER_CLK * sm_max * 1e6 / 1e12   # T lane-ops/s
+    mean_kernel_s = statistics.mean(kernel_ms) / 1e3
+    coll_per_launch = coll / args.steps
+    achieved = LANE_OPS_PER_COLLISION * coll_per_launch / mean_kernel_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "landed_per_s": landed_all / (total_ms_all / 1e3),
+        "config": {"workload": WORKLOAD, "particles_per_step_per_gpu": sc.total_particles,
+                   "instances": len(sc.instances), "grid": f"{sc.grid['nx']}x{sc.grid['ny']}",
+                   "tallies": "int64 counts + fp64 energy + int64 per-primitive landings",
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "seed": "distinct per step and per rank", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+                     "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
+                     "kernel": "transport_kernel", "kernel_ms_mean": statistics.mean(kernel_ms),
+                     "lane_ops_per_collision": LANE_OPS_PER_COLLISION,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz)"},
+        "e2e": {"value": (e2e_coll_all / e2e_t_all) if e2e_t_all > 0 else None, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons"),
+                   "samples": clk.get("samples"), "power_w_max": clk.get("power_w_max")},
+        "step_stats": {"collisions_per_step": coll / args.steps, "landed_per_step": landed / args.steps,
+                       "attempts_per_collision": sum(s["attempts"] for s in stats) / max(1, coll),
+                       "step_ms": step_ms},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--particles", type=int, default=10_000_000, help="per cathode")
+    ap.add_argument("--cpu-particles", type=int, default=600, help="oracle sample per cathode")
+    ap.add_argument("--ref-particles", type=int, default=400, help="oracle sample per cathode per step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

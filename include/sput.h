@@ -1,0 +1,298 @@
+/*
+ * sput.h -- C ABI of the GB300 sputtered-atom transport library (libsput.so).
+ *
+ * The library runs the per-particle Monte Carlo transport of sputtered atoms
+ * through the process gas described in Sec. "The SIMTRA model" of
+ * arXiv 2411.14413 (Thelen et al., pySIMTRA):
+ *   - launch point sampled from the racetrack profile (racetrack pdf),
+ *   - launch energy from the Thompson distribution with cut-off
+ *     E_max = k * Lambda * E_i - U_s, Lambda = 4 M_i M_t / (M_i + M_t)^2
+ *     (Eq. for phi(E)),
+ *   - launch direction from the six-term cosine sum
+ *     d2Y/dOmega = sum_{i=0..5} c_i cos^i(theta) (Eq. for d2Y/dOmega),
+ *   - free flights lambda = -lambda_m ln RN_1, RN_1 in ]0,1] (Eq. for lambda),
+ *     with lambda_m depending on the atom and gas velocities,
+ *   - after each flight a test whether the path reaches a surface ("dummy"
+ *     objects, the chamber and the cathodes), which deposits the atom,
+ *   - otherwise an elastic binary collision with a thermal gas atom under a
+ *     screened-Coulomb potential with Moliere screening,
+ * repeated until the atom lands; landings are tallied on a substrate grid
+ * together with arrival energy and angle.
+ *
+ * Readings where the paper gives no formula (all fixed here, see each field):
+ *   lambda_m(v) = v / (n_g <sigma(g) g>) averaged over a Maxwellian gas at T,
+ *   n_g = p / (k_B T); sigma = pi b_max^2 with the CM deflection at b_max equal
+ *   to chi_min; the gas partner is drawn from the Maxwellian weighted by
+ *   sigma(g) g (rejection against M(v) = max over g <= v + 6 sqrt(kT/m_gas) of
+ *   sigma(g) g, at most max_attempts attempts, the last attempt is kept);
+ *   impact parameter b = b_max sqrt(RN); azimuth 2 pi RN in the orthonormal
+ *   basis of Duff et al. (JCGT 2017); Firsov screening length
+ *   a = 0.8853 a_0 (Z1^1/2 + Z2^1/2)^(-2/3).
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = (seed low
+ * word, seed high word) and counter = (particle id, instance, event, block).
+ * Event 0 is the launch (block 0: racetrack radius, racetrack azimuth, energy,
+ * polar cosine; block 1 word 0: emission azimuth).  Event k >= 1 is flight k
+ * (block 0: flight length, impact parameter, scattering azimuth, acceptance
+ * of partner attempt 0; block 1+a: the three Maxwellian components of attempt
+ * a by Box-Muller; block 1+A+(a-1)/4 word (a-1)%4: acceptance of attempt a>=1,
+ * A = max_attempts).  A 32-bit word x maps to RN = ((x >> 8) + 1) * 2^-24.
+ * Every particle therefore has its own stream: integer tallies are bit-exact
+ * and independent of launch configuration, order and chunking.
+ *
+ * Units: mm, eV, u (atomic mass units), K, Pa, radians.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SPUT_OK (0) or an error code; no exception or signal ever
+ *     crosses the ABI, and a device error is reported, never trapped.
+ *   - Ownership: sput_scene handles are created and freed by the library.
+ *     Tally and record buffers are owned by the caller; the library never
+ *     frees or reallocates them.  Input arrays are copied during the call and
+ *     may be freed afterwards.
+ *   - Device pointers are plain CUDA device addresses on the scene's device;
+ *     `stream` is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef SPUT_H
+#define SPUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPUT_ABI_VERSION 1
+
+typedef enum sput_status {
+    SPUT_OK = 0,
+    SPUT_ERR_INVALID_ARG = 1,     /* NULL pointer, bad size, bad enum value */
+    SPUT_ERR_INVALID_SCENE = 2,   /* geometry / cathode / instance inconsistency */
+    SPUT_ERR_CUDA = 3,            /* a CUDA runtime call failed (message via sput_last_error) */
+    SPUT_ERR_TIMEOUT = 4,         /* host-side wait exceeded the caller's limit; device not reset */
+    SPUT_ERR_DEVICE_CHECK = 5,    /* the kernel raised a status bit (see sput_run_stats.device_status) */
+    SPUT_ERR_UNSUPPORTED = 6,     /* feature not available in this build */
+    SPUT_ERR_NO_MEMORY = 7        /* host or device allocation failed */
+} sput_status;
+
+/* Surface primitives (Sec. "The SIMTRA Python wrapper": chamber, magnetron
+ * body and "dummy" objects; every surface collects the atoms that reach it). */
+typedef enum sput_prim_kind {
+    SPUT_PRIM_BOX = 0,       /* the chamber box interior (sput_chamber.box_lo/hi); hit from inside */
+    SPUT_PRIM_RECT = 1,      /* plane rectangle: |(q-c).u| <= p0, |(q-c).v| <= p1, normal u x v */
+    SPUT_PRIM_DISC = 2,      /* plane disc / annulus: p0 <= |q-c| <= p1 in the (u, v) plane */
+    SPUT_PRIM_CYLINDER = 3   /* open tube: axis u through c, radius p0, |(q-c).u| <= p1 */
+} sput_prim_kind;
+
+typedef enum sput_interaction {
+    SPUT_INTERACTION_MOLIERE = 0,     /* screened Coulomb, Moliere screening (paper's choice) */
+    SPUT_INTERACTION_HARD_SPHERE = 1  /* test potential: diameter hs_diameter, chi = 2 acos(b/d) */
+} sput_interaction;
+
+typedef enum sput_gas_motion {
+    SPUT_GAS_THERMAL = 0,    /* Maxwellian gas at T (paper: gas motion taken into account) */
+    SPUT_GAS_STATIONARY = 1  /* gas atoms at rest (test mode) */
+} sput_gas_motion;
+
+typedef enum sput_count_type { SPUT_COUNT_INT32 = 0, SPUT_COUNT_INT64 = 1 } sput_count_type;
+
+typedef struct sput_chamber {
+    double box_lo[3], box_hi[3]; /* chamber interior, mm */
+    int gas_Z;                   /* process gas atomic number (Ar: 18) */
+    int reserved;
+    double gas_mass;             /* u */
+    double gas_T;                /* K, homogeneous gas in thermal equilibrium */
+} sput_chamber;
+
+typedef struct sput_primitive {
+    int kind;                    /* sput_prim_kind */
+    int reserved;
+    double center[3];
+    double u[3], v[3];           /* unit vectors (cylinder: u = axis, v unused) */
+    double p0, p1;               /* sizes, see sput_prim_kind */
+} sput_primitive;
+
+typedef struct sput_geometry {
+    int prim_begin, prim_count;  /* a contiguous range of the scene's primitives */
+    int substrate;               /* index (within the range) of the tallied RECT or DISC */
+    int reserved;
+} sput_geometry;
+
+typedef struct sput_cathode {
+    int Z;                       /* target element atomic number */
+    int target;                  /* index, within each geometry that uses it, of the target DISC */
+    double mass;                 /* u */
+    double U_s;                  /* surface binding energy, eV */
+    double center[3], normal[3], e1[3]; /* target-surface centre, outward unit normal, in-plane unit axis */
+    double rt_r0, rt_sigma, rt_R;       /* racetrack depth d(r) = exp(-(r-r0)^2/(2 sigma^2)) on [0, R];
+                                            radial pdf proportional to r d(r) (axisymmetric profile) */
+    double cos_coef[6];          /* c_0..c_5 of the emission cosine sum; (0,1,0,0,0,0) = cosine */
+} sput_cathode;
+
+typedef struct sput_instance {   /* one (cathode, process condition) pair */
+    int geometry, cathode;
+    double pressure;             /* Pa */
+    double E_i;                  /* incident ion energy, eV (set by the discharge voltage) */
+    double k;                    /* head-on factor of the cut-off, 0.4 in the paper */
+    uint64_t n_particles;        /* < 2^32 per instance */
+} sput_instance;
+
+typedef struct sput_grid {
+    int nx, ny;                  /* cells along substrate u and v */
+    double half_u, half_v;       /* grid covers [-half_u, half_u] x [-half_v, half_v] around the centre */
+    int count_type;              /* sput_count_type of the per-cell counts */
+    int n_ebins;                 /* arrival-energy histogram bins on [0, e_hist_max] (0 = off) */
+    double e_hist_max;           /* eV */
+    int n_abins;                 /* arrival-angle histogram bins on [0, 90] degrees (0 = off) */
+    int reserved;
+} sput_grid;
+
+typedef struct sput_physics {
+    double chi_min;              /* rad, CM deflection that defines sigma (default 1 degree) */
+    double hs_diameter;          /* Angstrom, hard-sphere test potential only */
+    int interaction;             /* sput_interaction */
+    int gas_motion;              /* sput_gas_motion */
+    int max_attempts;            /* partner rejection attempts per collision, 1..64 */
+    int reserved;
+    int64_t max_collisions;      /* per particle; beyond it the atom counts as timed out */
+} sput_physics;
+
+typedef struct sput_scene_desc {
+    uint32_t abi_version;        /* SPUT_ABI_VERSION */
+    int n_prims, n_geoms, n_cathodes, n_instances;
+    sput_chamber chamber;
+    const sput_primitive* prims;
+    const sput_geometry* geoms;
+    const sput_cathode* cathodes;
+    const sput_instance* instances;
+    sput_grid grid;
+    sput_physics physics;
+} sput_scene_desc;
+
+typedef struct sput_scene sput_scene;
+
+/* Per-particle record (optional), indexed by ticket = instance prefix + id. */
+typedef struct sput_record {
+    int32_t prim;                /* local primitive index hit, -1 = timed out */
+    int32_t cell;                /* substrate cell (front face), -1 otherwise */
+    float energy;                /* arrival energy, eV */
+    float cos_angle;             /* |cos| of the arrival angle to the substrate normal (front hits) */
+    uint32_t n_collisions;
+    float score;                 /* d ln p(path) / d ln n_gas, likelihood-ratio score */
+} sput_record;
+
+/* Caller-owned DEVICE buffers; NULL = not requested.  Layouts (row-major):
+ *   counts       [n_instances][ny][nx]   int32 or int64 (grid.count_type)
+ *   energy       [n_instances][ny][nx]   double, sum of arrival energies (eV)
+ *   score        [n_instances][ny][nx]   double, sum of the landing atoms' scores
+ *   prim_counts  [n_instances][max_prims] int64, landings per local primitive
+ *   timed_out    [n_instances]           int64
+ *   hist_E       [n_instances][n_ebins]  int64 (front substrate hits)
+ *   hist_A       [n_instances][n_abins]  int64 (front substrate hits)
+ *   records      [ticket_end - ticket_begin] sput_record, row = ticket - ticket_begin
+ * max_prims = the largest prim_count of any geometry; n_tickets = sum of n_particles;
+ * ticket = (sum of n_particles of the earlier instances) + particle id. */
+typedef struct sput_tallies {
+    void* counts;
+    double* energy;
+    double* score;
+    int64_t* prim_counts;
+    int64_t* timed_out;
+    int64_t* hist_E;
+    int64_t* hist_A;
+    sput_record* records;
+} sput_tallies;
+
+typedef struct sput_tally_layout {
+    int n_instances, nx, ny, max_prims, n_ebins, n_abins;
+    int count_type;
+    int reserved;
+    uint64_t n_tickets;
+} sput_tally_layout;
+
+typedef struct sput_run_opts {
+    uint64_t seed;
+    uint64_t ticket_begin, ticket_end; /* run tickets [begin, end); end = 0 means all */
+    int accumulate;              /* 0: zero the requested tallies first; 1: add into them */
+    int block_threads;           /* 0 = default (128); else a multiple of 32, <= 1024 */
+    int blocks_per_sm;           /* 0 = default (occupancy limit) */
+    int ticket_chunk;            /* tickets a warp takes per refill; 0 = default (32) */
+    int timeout_ms;              /* host wait limit when stats are requested; 0 = none */
+    int reserved;
+} sput_run_opts;
+
+typedef struct sput_run_stats {
+    uint64_t particles;          /* particles that completed (landed or timed out) */
+    uint64_t landed;
+    uint64_t timed_out;
+    uint64_t flights;            /* free flights (one per cycle) */
+    uint64_t collisions;         /* binary collisions */
+    uint64_t attempts;           /* partner rejection attempts */
+    uint32_t device_status;      /* bit mask of device checks, 0 = clean */
+    uint32_t grid_blocks;        /* launch shape that ran */
+    uint32_t block_threads;
+    float kernel_ms;             /* device time of the transport kernel (CUDA events) */
+} sput_run_stats;
+
+/* Library version (SPUT_ABI_VERSION) and status text. */
+int sput_version(void);
+const char* sput_status_str(sput_status s);
+/* Text of the last error on this thread (CUDA error string or validation message). */
+const char* sput_last_error(void);
+
+/* Validate the description, build the interaction tables (FP64 on the host:
+ * b_max(eps) and the head-on apsis in reduced Moliere units, <sigma g>(v) and
+ * the rejection bound M(v) per cathode/gas pair, racetrack guesses) and copy
+ * scene and tables to `device`.  On success *out owns device memory until
+ * sput_scene_destroy.  Errors: INVALID_ARG, INVALID_SCENE, CUDA, NO_MEMORY. */
+sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scene** out);
+
+/* Replace the instance table (pressures, ion energies, k, particle counts).
+ * The number of instances and each instance's geometry and cathode must stay
+ * the same (tables do not depend on them).  Synchronous host->device copy. */
+sput_status sput_instances_set(sput_scene* scene, const sput_instance* instances, int n_instances);
+
+/* Sizes of the tally buffers (see sput_tallies). */
+sput_status sput_tally_layout_get(const sput_scene* scene, sput_tally_layout* out);
+
+/* Transport the tickets of opts on `stream`.  Tallies are device pointers
+ * owned by the caller.  With stats == NULL the call only enqueues work (no
+ * host synchronisation).  With stats != NULL it waits for the kernel (at most
+ * opts->timeout_ms when > 0, else SPUT_ERR_TIMEOUT without touching the
+ * device) and fills the counters.  Concurrent runs of one scene on different
+ * streams race on the scene's scratch counters: serialise them. */
+sput_status sput_run(sput_scene* scene, const sput_run_opts* opts, void* stream, const sput_tallies* tallies,
+                     sput_run_stats* stats);
+
+/* Same as sput_run with HOST tally buffers (any subset non-NULL, same layouts):
+ * the library runs into scene-owned device buffers and copies the requested
+ * tallies back before returning.  Always synchronous. */
+sput_status sput_run_host(sput_scene* scene, const sput_run_opts* opts, const sput_tallies* host_tallies,
+                          sput_run_stats* stats);
+
+/* Free the scene and its device memory. */
+void sput_scene_destroy(sput_scene* scene);
+
+/* Diagnostics: evaluate one step of the device code path on given inputs
+ * (device functions identical to those of the transport kernel), for parity
+ * tests.  `x` and `y` are HOST arrays; layouts per `what`:
+ *   SPUT_PROBE_CHI      x[2n] = (eps, beta) reduced units, pair p -> y[n] = chi (rad)
+ *   SPUT_PROBE_BMAX     x[n]  = eps                        -> y[n] = b_max / a
+ *   SPUT_PROBE_K        x[n]  = speed (km/s), pair p       -> y[n] = <sigma g> (A^2 km/s)
+ *   SPUT_PROBE_M        x[n]  = speed (km/s), pair p       -> y[n] = M(v) (A^2 km/s)
+ *   SPUT_PROBE_LAUNCH   x[n]  = particle id, instance p    -> y[7n] = (x,y,z, dx,dy,dz, E)
+ * p is the pair index (one per cathode) or the instance index. */
+typedef enum sput_probe_kind {
+    SPUT_PROBE_CHI = 0,
+    SPUT_PROBE_BMAX = 1,
+    SPUT_PROBE_K = 2,
+    SPUT_PROBE_M = 3,
+    SPUT_PROBE_LAUNCH = 4
+} sput_probe_kind;
+
+sput_status sput_probe(sput_scene* scene, int what, int p, int n, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPUT_H */

@@ -491,6 +491,8 @@ static double K_of_v(const or_scene* S, const cath_t* c, double v)
 /* mean free path lambda_m(v) = v / (n_g K(v)), mm */
 static double lambda_m(const or_scene* S, const cath_t* c, const inst_t* I, double v)
 {
+    /* gas at rest: lambda_m = 1/(n_g sigma(v)), written without v/v */
+    if (S->gas_motion == GAS_STATIONARY) return 1.0 / (I->n_gas * sigma_of_g(S, c, v) * 1e-14);
     double K = K_of_v(S, c, v); /* Angstrom^2 km/s = 1e-14 mm^2 km/s */
     return v / (I->n_gas * K * 1e-14);
 }

@@ -1,0 +1,807 @@
+// sput_api.cpp -- C ABI of libsput.so: scene validation and packing, device
+// upload, launch of the transport kernel, statistics and diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sput.h"
+#include "sput_internal.h"
+#include "sput_tables.h"
+
+using namespace sput;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sput_status fail(sput_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+sput_status cuda_fail(cudaError_t e, const char* where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return SPUT_ERR_CUDA;
+}
+
+#define CUDA_TRY(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+void cross3(const double* a, const double* b, double* o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+bool unit3(const double* v) { return finite3(v) && std::fabs(dot3(v, v) - 1.0) < 1e-6; }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Thompson cut-off (Eq. for phi(E)): E_max = k Lambda E_i - U_s, Lambda = 4 M_i M_t / (M_i + M_t)^2
+double thompson_emax(double k, double Mi, double Mt, double Ei, double Us)
+{
+    return k * 4.0 * Mi * Mt / ((Mi + Mt) * (Mi + Mt)) * Ei - Us;
+}
+
+}  // namespace
+
+struct sput_scene {
+    int device = 0;
+    int n_sm = 0;
+    size_t smem_optin = 0;
+    sput_chamber chamber{};
+    sput_grid grid{};
+    sput_physics physics{};
+    std::vector<sput_primitive> prims;
+    std::vector<sput_geometry> geoms;
+    std::vector<sput_cathode> cathodes;
+    std::vector<sput_instance> instances;
+    // packed host copies
+    std::vector<DevPrim> dprims;
+    std::vector<DevGeom> dgeoms;
+    std::vector<DevCathode> dcath;
+    std::vector<DevPair> dpairs;
+    std::vector<DevInstance> dinst;
+    std::vector<unsigned long long> prefix;
+    std::vector<float4> wtab;
+    std::vector<float> rt;
+    std::vector<PairPhys> pair_phys;
+    std::vector<int> pair_monotone;
+    std::vector<double> pair_E_top;
+    const BmaxTable* bt = nullptr;
+    double s_gas = 0.0;
+    int max_prims = 0;
+    unsigned long long n_tickets = 0;
+    // device memory
+    unsigned char* d_blob = nullptr;
+    size_t off_prims = 0, off_geoms = 0, off_cath = 0, off_pairs = 0, off_inst = 0, off_prefix = 0, off_bm = 0,
+           off_xh = 0, off_w = 0, off_rt = 0, blob_bytes = 0;
+    // run scratch (allocated on the first run): ticket counter, stats, status word
+    unsigned long long* d_scratch = nullptr;
+    unsigned long long* h_scratch = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // device staging of sput_run_host
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t own_stream = nullptr;
+    Params base{};
+};
+
+namespace {
+
+sput_status validate(const sput_scene_desc* d)
+{
+    if (!d) return fail(SPUT_ERR_INVALID_ARG, "desc is NULL");
+    if (d->abi_version != SPUT_ABI_VERSION) return fail(SPUT_ERR_INVALID_ARG, "abi_version mismatch");
+    if (d->n_prims < 1 || d->n_geoms < 1 || d->n_cathodes < 1 || d->n_instances < 1)
+        return fail(SPUT_ERR_INVALID_ARG, "scene needs at least one primitive, geometry, cathode and instance");
+    if (!d->prims || !d->geoms || !d->cathodes || !d->instances)
+        return fail(SPUT_ERR_INVALID_ARG, "NULL scene array");
+    const sput_chamber& ch = d->chamber;
+    for (int a = 0; a < 3; ++a)
+        if (!(ch.box_lo[a] < ch.box_hi[a])) return fail(SPUT_ERR_INVALID_SCENE, "chamber box_lo must be < box_hi");
+    if (ch.gas_Z < 1 || !(ch.gas_mass > 0.0) || !(ch.gas_T > 0.0) || !std::isfinite(ch.gas_T))
+        return fail(SPUT_ERR_INVALID_SCENE, "gas Z, mass and temperature must be positive");
+    for (int i = 0; i < d->n_prims; ++i) {
+        const sput_primitive& P = d->prims[i];
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "primitive %d: ", i);
+        if (P.kind < SPUT_PRIM_BOX || P.kind > SPUT_PRIM_CYLINDER) return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "bad kind");
+        if (P.kind == SPUT_PRIM_BOX) continue;
+        if (!finite3(P.center) || !unit3(P.u)) return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "centre/axis not finite or u not unit");
+        if (!(P.p0 >= 0.0) || !(P.p1 > 0.0) || !std::isfinite(P.p0) || !std::isfinite(P.p1))
+            return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "sizes must be finite, p0 >= 0, p1 > 0");
+        if (P.kind == SPUT_PRIM_RECT || P.kind == SPUT_PRIM_DISC) {
+            if (!unit3(P.v) || std::fabs(dot3(P.u, P.v)) > 1e-6) return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "v must be unit and orthogonal to u");
+            if (P.kind == SPUT_PRIM_RECT && !(P.p0 > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "rect half sizes must be > 0");
+            if (P.kind == SPUT_PRIM_DISC && !(P.p0 < P.p1)) return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "disc needs inner radius < outer radius");
+        }
+        if (P.kind == SPUT_PRIM_CYLINDER && !(P.p0 > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, std::string(buf) + "cylinder radius must be > 0");
+    }
+    for (int g = 0; g < d->n_geoms; ++g) {
+        const sput_geometry& G = d->geoms[g];
+        if (G.prim_begin < 0 || G.prim_count < 1 || G.prim_begin + G.prim_count > d->n_prims)
+            return fail(SPUT_ERR_INVALID_SCENE, "geometry primitive range out of bounds");
+        if (G.substrate < 0 || G.substrate >= G.prim_count) return fail(SPUT_ERR_INVALID_SCENE, "substrate index outside the geometry");
+        int k = d->prims[G.prim_begin + G.substrate].kind;
+        if (k != SPUT_PRIM_RECT && k != SPUT_PRIM_DISC) return fail(SPUT_ERR_INVALID_SCENE, "substrate must be a RECT or DISC");
+    }
+    for (int c = 0; c < d->n_cathodes; ++c) {
+        const sput_cathode& C = d->cathodes[c];
+        if (C.Z < 1 || !(C.mass > 0.0) || !(C.U_s > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "cathode Z, mass, U_s must be positive");
+        if (!finite3(C.center) || !unit3(C.normal) || !unit3(C.e1) || std::fabs(dot3(C.normal, C.e1)) > 1e-6)
+            return fail(SPUT_ERR_INVALID_SCENE, "cathode pose: normal and e1 must be orthonormal");
+        if (!(C.rt_sigma > 0.0) || !(C.rt_R > 0.0) || !(C.rt_r0 >= 0.0) || !std::isfinite(C.rt_r0))
+            return fail(SPUT_ERR_INVALID_SCENE, "racetrack needs sigma > 0, R > 0, r0 >= 0");
+        double sum = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            if (!(C.cos_coef[i] >= 0.0) || !std::isfinite(C.cos_coef[i])) return fail(SPUT_ERR_INVALID_SCENE, "cosine coefficients must be >= 0");
+            sum += C.cos_coef[i];
+        }
+        if (!(sum > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "cosine coefficients must not all be zero");
+    }
+    const sput_grid& gr = d->grid;
+    if (gr.nx < 1 || gr.ny < 1 || !(gr.half_u > 0.0) || !(gr.half_v > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "grid needs nx, ny >= 1 and positive extent");
+    if ((long long)gr.nx * gr.ny > (1LL << 30)) return fail(SPUT_ERR_INVALID_SCENE, "grid too large");
+    if (gr.count_type != SPUT_COUNT_INT32 && gr.count_type != SPUT_COUNT_INT64) return fail(SPUT_ERR_INVALID_SCENE, "bad count_type");
+    if (gr.n_ebins < 0 || gr.n_abins < 0 || (gr.n_ebins > 0 && !(gr.e_hist_max > 0.0))) return fail(SPUT_ERR_INVALID_SCENE, "bad histogram settings");
+    const sput_physics& ph = d->physics;
+    if (!(ph.chi_min > 0.0 && ph.chi_min < kPi)) return fail(SPUT_ERR_INVALID_SCENE, "chi_min must lie in (0, pi)");
+    if (ph.interaction != SPUT_INTERACTION_MOLIERE && ph.interaction != SPUT_INTERACTION_HARD_SPHERE) return fail(SPUT_ERR_INVALID_SCENE, "bad interaction");
+    if (ph.interaction == SPUT_INTERACTION_HARD_SPHERE && !(ph.hs_diameter > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "hard-sphere diameter must be > 0");
+    if (ph.gas_motion != SPUT_GAS_THERMAL && ph.gas_motion != SPUT_GAS_STATIONARY) return fail(SPUT_ERR_INVALID_SCENE, "bad gas_motion");
+    if (ph.max_attempts < 1 || ph.max_attempts > 64) return fail(SPUT_ERR_INVALID_SCENE, "max_attempts must be 1..64");
+    if (ph.max_collisions < 0 || ph.max_collisions > 0xFFFFFFF0LL) return fail(SPUT_ERR_INVALID_SCENE, "max_collisions out of range");
+    return SPUT_OK;
+}
+
+sput_status validate_instances(const sput_scene* S, const sput_instance* inst, int n, const sput_cathode* cath,
+                               int n_cath, const sput_geometry* geoms, int n_geoms, const sput_primitive* prims,
+                               int count_type)
+{
+    unsigned long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        const sput_instance& I = inst[i];
+        if (I.geometry < 0 || I.geometry >= n_geoms || I.cathode < 0 || I.cathode >= n_cath)
+            return fail(SPUT_ERR_INVALID_SCENE, "instance geometry/cathode index out of range");
+        const sput_cathode& C = cath[I.cathode];
+        const sput_geometry& G = geoms[I.geometry];
+        if (C.target < 0 || C.target >= G.prim_count || prims[G.prim_begin + C.target].kind != SPUT_PRIM_DISC)
+            return fail(SPUT_ERR_INVALID_SCENE, "cathode target must be a DISC of the instance geometry");
+        if (!(I.pressure >= 0.0) || !std::isfinite(I.pressure) || !(I.E_i > 0.0) || !(I.k > 0.0))
+            return fail(SPUT_ERR_INVALID_SCENE, "instance needs pressure >= 0, E_i > 0, k > 0");
+        if (I.n_particles >= (1ull << 32)) return fail(SPUT_ERR_INVALID_SCENE, "more than 2^32-1 particles in one instance");
+        total += I.n_particles;
+    }
+    if (count_type == SPUT_COUNT_INT32 && total > 0x7FFFFFFFull) return fail(SPUT_ERR_INVALID_SCENE, "int32 counts need fewer than 2^31 particles");
+    (void)S;
+    return SPUT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sput_version(void) { return SPUT_ABI_VERSION; }
+
+const char* sput_status_str(sput_status s)
+{
+    switch (s) {
+    case SPUT_OK: return "ok";
+    case SPUT_ERR_INVALID_ARG: return "invalid argument";
+    case SPUT_ERR_INVALID_SCENE: return "invalid scene";
+    case SPUT_ERR_CUDA: return "CUDA error";
+    case SPUT_ERR_TIMEOUT: return "timeout";
+    case SPUT_ERR_DEVICE_CHECK: return "device check failed";
+    case SPUT_ERR_UNSUPPORTED: return "unsupported";
+    case SPUT_ERR_NO_MEMORY: return "out of memory";
+    }
+    return "unknown status";
+}
+
+const char* sput_last_error(void) { return g_last_error.c_str(); }
+
+static sput_status pack_instances(sput_scene* S)
+{
+    const double kT = kBoltzmannJ * S->chamber.gas_T;
+    S->dinst.assign(S->instances.size(), DevInstance{});
+    S->prefix.assign(S->instances.size() + 1, 0ull);
+    for (size_t i = 0; i < S->instances.size(); ++i) {
+        const sput_instance& I = S->instances[i];
+        const sput_cathode& C = S->cathodes[I.cathode];
+        double Em = thompson_emax(I.k, S->chamber.gas_mass, C.mass, I.E_i, C.U_s);
+        if (!(Em > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "E_max = k Lambda E_i - U_s must be > 0");
+        int pair = S->dcath[I.cathode].pair;
+        if (Em > S->pair_E_top[pair] * (1.0 + 1e-12))
+            return fail(SPUT_ERR_INVALID_ARG, "E_max beyond the range of the scene's tables; recreate the scene");
+        DevInstance& D = S->dinst[i];
+        D.geometry = I.geometry;
+        D.cathode = I.cathode;
+        D.pair = pair;
+        D.n = (uint32_t)I.n_particles;
+        // n_g = p / (k_B T) in m^-3 -> mm^-3 (1e-9); sigma in A^2 -> mm^2 (1e-14)
+        D.ng14 = (float)(I.pressure / kT * 1e-9 * 1e-14);
+        D.thompson_q = (float)(Em / (Em + C.U_s));
+        D.U_s = (float)C.U_s;
+        D.ticket_begin = S->prefix[i];
+        S->prefix[i + 1] = S->prefix[i] + I.n_particles;
+    }
+    S->n_tickets = S->prefix.back();
+    return SPUT_OK;
+}
+
+sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scene** out)
+{
+    if (!out) return fail(SPUT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sput_status st = validate(desc);
+    if (st != SPUT_OK) return st;
+    st = validate_instances(nullptr, desc->instances, desc->n_instances, desc->cathodes, desc->n_cathodes, desc->geoms,
+                            desc->n_geoms, desc->prims, desc->grid.count_type);
+    if (st != SPUT_OK) return st;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SPUT_ERR_INVALID_ARG, "device index out of range");
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(SPUT_ERR_CUDA, "cudaSetDevice failed");
+
+    sput_scene* S = new sput_scene();
+    S->device = device;
+    CUDA_TRY(cudaDeviceGetAttribute(&S->n_sm, cudaDevAttrMultiProcessorCount, device));
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    S->smem_optin = (size_t)optin;
+    S->chamber = desc->chamber;
+    S->grid = desc->grid;
+    S->physics = desc->physics;
+    S->prims.assign(desc->prims, desc->prims + desc->n_prims);
+    S->geoms.assign(desc->geoms, desc->geoms + desc->n_geoms);
+    S->cathodes.assign(desc->cathodes, desc->cathodes + desc->n_cathodes);
+    S->instances.assign(desc->instances, desc->instances + desc->n_instances);
+
+    const bool hard = S->physics.interaction == SPUT_INTERACTION_HARD_SPHERE;
+    const int thermal = S->physics.gas_motion == SPUT_GAS_THERMAL;
+    S->s_gas = std::sqrt(kBoltzmannEV * S->chamber.gas_T / (S->chamber.gas_mass * kEnergyUnit));
+    S->bt = hard ? nullptr : &bmax_table(S->physics.chi_min);
+
+    // primitives
+    S->dprims.resize(S->prims.size());
+    for (size_t i = 0; i < S->prims.size(); ++i) {
+        const sput_primitive& P = S->prims[i];
+        DevPrim& D = S->dprims[i];
+        double n[3];
+        cross3(P.u, P.v, n);
+        D.cx = (float)P.center[0];
+        D.cy = (float)P.center[1];
+        D.cz = (float)P.center[2];
+        D.kind = P.kind;
+        D.ux = (float)P.u[0];
+        D.uy = (float)P.u[1];
+        D.uz = (float)P.u[2];
+        D.p0 = (float)P.p0;
+        D.vx = (float)P.v[0];
+        D.vy = (float)P.v[1];
+        D.vz = (float)P.v[2];
+        D.p1 = (float)P.p1;
+        D.nx = (float)n[0];
+        D.ny = (float)n[1];
+        D.nz = (float)n[2];
+        D.p0sq = (float)(P.p0 * P.p0);
+    }
+    S->dgeoms.resize(S->geoms.size());
+    S->max_prims = 0;
+    for (size_t g = 0; g < S->geoms.size(); ++g) {
+        S->dgeoms[g] = DevGeom{S->geoms[g].prim_begin, S->geoms[g].prim_count, S->geoms[g].substrate, 0};
+        S->max_prims = std::max(S->max_prims, S->geoms[g].prim_count);
+    }
+
+    // interaction pairs (one per distinct cathode element) and their E range
+    std::map<std::pair<int, double>, int> pair_of;
+    std::vector<int> cath_pair(S->cathodes.size());
+    for (size_t c = 0; c < S->cathodes.size(); ++c) {
+        auto key = std::make_pair(S->cathodes[c].Z, S->cathodes[c].mass);
+        auto it = pair_of.find(key);
+        if (it == pair_of.end()) {
+            int id = (int)S->pair_phys.size();
+            pair_of[key] = id;
+            S->pair_phys.push_back(make_pair(S->cathodes[c].Z, S->cathodes[c].mass, S->chamber.gas_Z,
+                                             S->chamber.gas_mass, hard ? 1 : 0, S->physics.hs_diameter,
+                                             S->physics.chi_min));
+            S->pair_E_top.push_back(0.0);
+            cath_pair[c] = id;
+        } else {
+            cath_pair[c] = it->second;
+        }
+    }
+    for (const sput_instance& I : S->instances) {
+        const sput_cathode& C = S->cathodes[I.cathode];
+        double Em = thompson_emax(I.k, S->chamber.gas_mass, C.mass, I.E_i, C.U_s);
+        double& top = S->pair_E_top[cath_pair[I.cathode]];
+        top = std::max(top, std::max(2.0 * Em, 200.0));
+    }
+    S->dpairs.resize(S->pair_phys.size());
+    S->pair_monotone.resize(S->pair_phys.size());
+    const double h_w = 0.02;
+    for (size_t p = 0; p < S->pair_phys.size(); ++p) {
+        const PairPhys& pp = S->pair_phys[p];
+        double v_top = std::sqrt(2.0 * S->pair_E_top[p] / (pp.m1 * kEnergyUnit)) + 12.0 * S->s_gas;
+        std::vector<float4> K, M;
+        int n_w = 0;
+        build_w_tables(pp, S->bt, S->s_gas, thermal, v_top, h_w, K, M, n_w);
+        DevPair& D = S->dpairs[p];
+        D.kappa = (float)pp.kappa;
+        D.ln_kappa = (float)std::log(pp.kappa);
+        D.sigma_scale = (float)(hard ? kPi * pp.hs_d * pp.hs_d : kPi * pp.a * pp.a);
+        D.m1M = (float)(pp.m1 / (pp.m1 + pp.m2));
+        D.m2M = (float)(pp.m2 / (pp.m1 + pp.m2));
+        D.hard_sphere = hard ? 1 : 0;
+        D.K_off = (int)S->wtab.size();
+        S->wtab.insert(S->wtab.end(), K.begin(), K.end());
+        D.M_off = (int)S->wtab.size();
+        S->wtab.insert(S->wtab.end(), M.begin(), M.end());
+        D.n_w = n_w;
+        D.w_inv_h = (float)(1.0 / h_w);
+        D.inv_s = (float)(1.0 / S->s_gas);
+        S->pair_monotone[p] = h_monotone(pp, S->bt, v_top + 20.0 * S->s_gas);
+    }
+
+    // cathodes
+    const int rt_n = 256;
+    S->dcath.resize(S->cathodes.size());
+    S->rt.resize(S->cathodes.size() * (rt_n + 1));
+    for (size_t c = 0; c < S->cathodes.size(); ++c) {
+        const sput_cathode& C = S->cathodes[c];
+        DevCathode& D = S->dcath[c];
+        double e2[3];
+        cross3(C.normal, C.e1, e2);
+        for (int a = 0; a < 3; ++a) {
+            D.c[a] = (float)C.center[a];
+            D.n[a] = (float)C.normal[a];
+            D.e1[a] = (float)C.e1[a];
+            D.e2[a] = (float)e2[a];
+        }
+        const double k = 1.0 / (C.rt_sigma * std::sqrt(2.0));
+        D.rt_r0 = (float)C.rt_r0;
+        D.rt_R = (float)C.rt_R;
+        D.rt_k = (float)k;
+        D.rt_A = (float)(C.rt_sigma * C.rt_sigma);
+        D.rt_C = (float)std::exp(-C.rt_r0 * C.rt_r0 * k * k);
+        D.rt_B = (float)(C.rt_r0 * C.rt_sigma * std::sqrt(kPi / 2.0));
+        D.rt_E0 = (float)std::erf(C.rt_r0 * k);
+        D.rt_FR = (float)racetrack_F64(C.rt_r0, C.rt_sigma, C.rt_R);
+        double norm = 0.0;
+        bool pure = true;
+        for (int i = 0; i < 6; ++i) {
+            D.coef[i] = (float)C.cos_coef[i];
+            norm += C.cos_coef[i] / (i + 1);
+            if (C.cos_coef[i] != (i == 1 ? 1.0 : 0.0)) pure = false;
+        }
+        D.coef_norm = (float)norm;
+        D.cos_general = pure ? 0 : 1;
+        D.target = C.target;
+        D.pair = cath_pair[c];
+        D.rt_tab = (int)(c * (rt_n + 1));
+        racetrack_guess(C.rt_r0, C.rt_sigma, C.rt_R, rt_n, &S->rt[c * (rt_n + 1)]);
+        D.v_per_sqrtE = (float)std::sqrt(2.0 / (C.mass * kEnergyUnit));
+        D.E_per_v2 = (float)(0.5 * C.mass * kEnergyUnit);
+    }
+    st = pack_instances(S);
+    if (st != SPUT_OK) {
+        delete S;
+        return st;
+    }
+
+    // one device allocation for every table
+    size_t o = 0;
+    auto place = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    S->off_prims = place(sizeof(DevPrim) * S->dprims.size());
+    S->off_geoms = place(sizeof(DevGeom) * S->dgeoms.size());
+    S->off_cath = place(sizeof(DevCathode) * S->dcath.size());
+    S->off_pairs = place(sizeof(DevPair) * S->dpairs.size());
+    S->off_inst = place(sizeof(DevInstance) * S->dinst.size());
+    S->off_prefix = place(sizeof(unsigned long long) * S->prefix.size());
+    const BmaxTable* bt = S->bt;
+    std::vector<float4> bm_hs(1, make_float4(1.0f, 0.0f, 0.0f, 0.0f));
+    std::vector<float> xh_hs(2, 0.0f);
+    const std::vector<float4>& bm = bt ? bt->cubic : bm_hs;
+    const std::vector<float>& xh = bt ? bt->xh : xh_hs;
+    S->off_bm = place(sizeof(float4) * bm.size());
+    S->off_xh = place(sizeof(float) * xh.size());
+    S->off_w = place(sizeof(float4) * S->wtab.size());
+    S->off_rt = place(sizeof(float) * S->rt.size());
+    S->blob_bytes = o;
+    cudaError_t e = cudaMalloc(&S->d_blob, S->blob_bytes);
+    if (e != cudaSuccess) {
+        delete S;
+        return fail(SPUT_ERR_NO_MEMORY, std::string("cudaMalloc scene: ") + cudaGetErrorString(e));
+    }
+    std::vector<unsigned char> h(S->blob_bytes, 0);
+    auto put = [&](size_t off, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(h.data() + off, src, bytes);
+    };
+    put(S->off_prims, S->dprims.data(), sizeof(DevPrim) * S->dprims.size());
+    put(S->off_geoms, S->dgeoms.data(), sizeof(DevGeom) * S->dgeoms.size());
+    put(S->off_cath, S->dcath.data(), sizeof(DevCathode) * S->dcath.size());
+    put(S->off_pairs, S->dpairs.data(), sizeof(DevPair) * S->dpairs.size());
+    put(S->off_inst, S->dinst.data(), sizeof(DevInstance) * S->dinst.size());
+    put(S->off_prefix, S->prefix.data(), sizeof(unsigned long long) * S->prefix.size());
+    put(S->off_bm, bm.data(), sizeof(float4) * bm.size());
+    put(S->off_xh, xh.data(), sizeof(float) * xh.size());
+    put(S->off_w, S->wtab.data(), sizeof(float4) * S->wtab.size());
+    put(S->off_rt, S->rt.data(), sizeof(float) * S->rt.size());
+    e = cudaMemcpy(S->d_blob, h.data(), S->blob_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_scratch, 64);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
+    if (e != cudaSuccess) {
+        sput_scene_destroy(S);
+        return cuda_fail(e, "scene upload");
+    }
+
+    Params& p = S->base;
+    std::memset(&p, 0, sizeof p);
+    p.prims = reinterpret_cast<const DevPrim*>(S->d_blob + S->off_prims);
+    p.geoms = reinterpret_cast<const DevGeom*>(S->d_blob + S->off_geoms);
+    p.cath = reinterpret_cast<const DevCathode*>(S->d_blob + S->off_cath);
+    p.pairs = reinterpret_cast<const DevPair*>(S->d_blob + S->off_pairs);
+    p.inst = reinterpret_cast<const DevInstance*>(S->d_blob + S->off_inst);
+    p.prefix = reinterpret_cast<const unsigned long long*>(S->d_blob + S->off_prefix);
+    p.bm_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_bm);
+    p.xh_tab = reinterpret_cast<const float*>(S->d_blob + S->off_xh);
+    p.w_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_w);
+    p.rt_tab = reinterpret_cast<const float*>(S->d_blob + S->off_rt);
+    p.n_prims = (int)S->dprims.size();
+    p.n_geoms = (int)S->dgeoms.size();
+    p.n_pairs = (int)S->dpairs.size();
+    p.n_inst = (int)S->dinst.size();
+    p.n_bm = (int)bm.size();
+    p.n_w_total = (int)S->wtab.size();
+    p.bm_lo = bt ? (float)bt->lo : 0.0f;
+    p.bm_inv_h = bt ? (float)(1.0 / bt->h) : 1.0f;
+    for (int a = 0; a < 3; ++a) {
+        p.box_lo[a] = (float)S->chamber.box_lo[a];
+        p.box_hi[a] = (float)S->chamber.box_hi[a];
+    }
+    p.s_gas = (float)S->s_gas;
+    p.gas_thermal = thermal;
+    p.max_attempts = S->physics.max_attempts;
+    p.max_prims = S->max_prims;
+    p.max_collisions = S->physics.max_collisions;
+    p.rt_n = rt_n;
+    p.nx = S->grid.nx;
+    p.ny = S->grid.ny;
+    p.half_u = (float)S->grid.half_u;
+    p.half_v = (float)S->grid.half_v;
+    p.cells_per_mm_u = (float)(S->grid.nx / (2.0 * S->grid.half_u));
+    p.cells_per_mm_v = (float)(S->grid.ny / (2.0 * S->grid.half_v));
+    p.n_ebins = S->grid.n_ebins;
+    p.n_abins = S->grid.n_abins;
+    p.ebin_per_eV = S->grid.n_ebins > 0 ? (float)(S->grid.n_ebins / S->grid.e_hist_max) : 0.0f;
+    // Gauss-Mehler constants: theta_j = (2j-1) pi / (2N), j = 1..N/2
+    for (int j = 0; j < kGMHalf; ++j) {
+        double th = (2.0 * (j + 1) - 1.0) * kPi / (2.0 * kGMNodes);
+        double c = std::cos(th), s = std::sin(th);
+        p.gm[j] = make_float4((float)c, (float)(1.0 / (1.0 + c)), (float)(c / (s * s)),
+                              (float)(2.0 * std::sin(0.5 * th) * std::sin(0.5 * th) / c));
+    }
+    if (transport_configure((int)S->smem_optin) != 0) {
+        sput_scene_destroy(S);
+        return fail(SPUT_ERR_CUDA, "cudaFuncSetAttribute on the transport kernel failed");
+    }
+    // privatise per-primitive counters in shared memory while they fit
+    p.smem_counters = (size_t)p.n_inst * (p.max_prims + 1) <= 12288 ? 1 : 0;
+    if (transport_smem_bytes(p) > S->smem_optin) {
+        p.smem_counters = 0;
+        if (transport_smem_bytes(p) > S->smem_optin) {
+            sput_scene_destroy(S);
+            return fail(SPUT_ERR_UNSUPPORTED, "scene tables exceed the shared memory of one block");
+        }
+    }
+    *out = S;
+    return SPUT_OK;
+}
+
+sput_status sput_instances_set(sput_scene* S, const sput_instance* instances, int n)
+{
+    if (!S || !instances) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    if (n != (int)S->instances.size()) return fail(SPUT_ERR_INVALID_ARG, "number of instances must not change");
+    for (int i = 0; i < n; ++i)
+        if (instances[i].geometry != S->instances[i].geometry || instances[i].cathode != S->instances[i].cathode)
+            return fail(SPUT_ERR_INVALID_ARG, "instance geometry and cathode must not change");
+    sput_status st = validate_instances(S, instances, n, S->cathodes.data(), (int)S->cathodes.size(), S->geoms.data(),
+                                        (int)S->geoms.size(), S->prims.data(), S->grid.count_type);
+    if (st != SPUT_OK) return st;
+    std::vector<sput_instance> old = S->instances;
+    S->instances.assign(instances, instances + n);
+    st = pack_instances(S);
+    if (st != SPUT_OK) {
+        S->instances = old;
+        pack_instances(S);
+        return st;
+    }
+    DeviceGuard guard(S->device);
+    CUDA_TRY(cudaMemcpy(S->d_blob + S->off_inst, S->dinst.data(), sizeof(DevInstance) * S->dinst.size(),
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(S->d_blob + S->off_prefix, S->prefix.data(), sizeof(unsigned long long) * S->prefix.size(),
+                        cudaMemcpyHostToDevice));
+    return SPUT_OK;
+}
+
+sput_status sput_tally_layout_get(const sput_scene* S, sput_tally_layout* out)
+{
+    if (!S || !out) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    out->n_instances = (int)S->instances.size();
+    out->nx = S->grid.nx;
+    out->ny = S->grid.ny;
+    out->max_prims = S->max_prims;
+    out->n_ebins = S->grid.n_ebins;
+    out->n_abins = S->grid.n_abins;
+    out->count_type = S->grid.count_type;
+    out->reserved = 0;
+    out->n_tickets = S->n_tickets;
+    return SPUT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct TallySizes {
+    size_t counts, energy, score, prim_counts, timed_out, hist_E, hist_A;
+};
+
+TallySizes tally_sizes(const sput_scene* S)
+{
+    const size_t ni = S->instances.size(), nc = (size_t)S->grid.nx * S->grid.ny;
+    TallySizes t;
+    t.counts = ni * nc * (S->grid.count_type == SPUT_COUNT_INT64 ? 8 : 4);
+    t.energy = ni * nc * 8;
+    t.score = ni * nc * 8;
+    t.prim_counts = ni * S->max_prims * 8;
+    t.timed_out = ni * 8;
+    t.hist_E = ni * S->grid.n_ebins * 8;
+    t.hist_A = ni * S->grid.n_abins * 8;
+    return t;
+}
+
+sput_status ensure_scratch(sput_scene* S)
+{
+    if (S->d_scratch) return SPUT_OK;
+    cudaError_t e = cudaMalloc(&S->d_scratch, 64);
+    if (e != cudaSuccess) return fail(SPUT_ERR_NO_MEMORY, std::string("cudaMalloc scratch: ") + cudaGetErrorString(e));
+    return SPUT_OK;
+}
+
+sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stream, const sput_tallies* T,
+                     sput_run_stats* stats, unsigned long long* scratch)
+{
+    if (!opts || !T) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    if (T->hist_E && S->grid.n_ebins == 0) return fail(SPUT_ERR_INVALID_ARG, "hist_E requested but n_ebins = 0");
+    if (T->hist_A && S->grid.n_abins == 0) return fail(SPUT_ERR_INVALID_ARG, "hist_A requested but n_abins = 0");
+    unsigned long long tb = opts->ticket_begin, te = opts->ticket_end ? opts->ticket_end : S->n_tickets;
+    if (tb > te || te > S->n_tickets) return fail(SPUT_ERR_INVALID_ARG, "ticket range outside [0, n_tickets]");
+    int threads = opts->block_threads ? opts->block_threads : 128;
+    if (threads < 32 || threads > 256 || threads % 32) return fail(SPUT_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+    int chunk = opts->ticket_chunk ? opts->ticket_chunk : 32;
+    if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
+
+    Params p = S->base;
+    p.counts = T->counts;
+    p.energy = T->energy;
+    p.score = T->score;
+    p.prim_counts = reinterpret_cast<long long*>(T->prim_counts);
+    p.timed_out = reinterpret_cast<long long*>(T->timed_out);
+    p.hist_E = reinterpret_cast<long long*>(T->hist_E);
+    p.hist_A = reinterpret_cast<long long*>(T->hist_A);
+    p.records = T->records;
+    p.key0 = (uint32_t)opts->seed;
+    p.key1 = (uint32_t)(opts->seed >> 32);
+    p.ticket_begin = tb;
+    p.ticket_end = te;
+    p.chunk = chunk;
+    p.ticket_counter = scratch;
+    p.stats = scratch + 1;
+    p.status = reinterpret_cast<unsigned int*>(scratch + 1 + kNumStats);
+
+    const TallySizes sz = tally_sizes(S);
+    if (!opts->accumulate) {
+        if (T->counts) CUDA_TRY(cudaMemsetAsync(T->counts, 0, sz.counts, stream));
+        if (T->energy) CUDA_TRY(cudaMemsetAsync(T->energy, 0, sz.energy, stream));
+        if (T->score) CUDA_TRY(cudaMemsetAsync(T->score, 0, sz.score, stream));
+        if (T->prim_counts) CUDA_TRY(cudaMemsetAsync(T->prim_counts, 0, sz.prim_counts, stream));
+        if (T->timed_out) CUDA_TRY(cudaMemsetAsync(T->timed_out, 0, sz.timed_out, stream));
+        if (T->hist_E) CUDA_TRY(cudaMemsetAsync(T->hist_E, 0, sz.hist_E, stream));
+        if (T->hist_A) CUDA_TRY(cudaMemsetAsync(T->hist_A, 0, sz.hist_A, stream));
+    }
+    CUDA_TRY(cudaMemsetAsync(scratch, 0, 64, stream));
+
+    const int c64 = S->grid.count_type == SPUT_COUNT_INT64;
+    const size_t smem = transport_smem_bytes(p);
+    int bps = transport_max_blocks_per_sm(c64, threads, smem);
+    if (bps < 1) return fail(SPUT_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+    if (opts->blocks_per_sm > 0) bps = std::min(bps, opts->blocks_per_sm);
+    unsigned long long need = (te - tb + threads - 1) / threads;
+    int blocks = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>((unsigned long long)S->n_sm * bps, need));
+    if (te == tb) blocks = 1;
+    CUDA_TRY(cudaEventRecord(S->ev0, stream));
+    int le = transport_launch(p, c64, blocks, threads, smem, stream);
+    if (le != 0) return cuda_fail((cudaError_t)le, "transport kernel launch");
+    CUDA_TRY(cudaEventRecord(S->ev1, stream));
+    if (!stats) return SPUT_OK;
+
+    CUDA_TRY(cudaMemcpyAsync(S->h_scratch, scratch, 64, cudaMemcpyDeviceToHost, stream));
+    cudaEvent_t done;
+    CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(done, stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(done);
+        return cuda_fail(e, "cudaEventRecord");
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaEventDestroy(done);
+            return cuda_fail(e, "transport kernel");
+        }
+        if (opts->timeout_ms > 0 &&
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+                opts->timeout_ms) {
+            cudaEventDestroy(done);
+            return fail(SPUT_ERR_TIMEOUT, "transport did not finish within timeout_ms (device left running)");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(done);
+    const unsigned long long* h = S->h_scratch;
+    stats->particles = h[1];
+    stats->landed = h[2];
+    stats->timed_out = h[3];
+    stats->flights = h[4];
+    stats->collisions = h[5];
+    stats->attempts = h[6];
+    stats->device_status = (uint32_t)(h[1 + kNumStats] & 0xffffffffu);
+    stats->grid_blocks = (uint32_t)blocks;
+    stats->block_threads = (uint32_t)threads;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+    stats->kernel_ms = ms;
+    if (stats->device_status) return fail(SPUT_ERR_DEVICE_CHECK, "device status bits set");
+    return SPUT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sput_status sput_run(sput_scene* S, const sput_run_opts* opts, void* stream, const sput_tallies* T,
+                     sput_run_stats* stats)
+{
+    if (!S) return fail(SPUT_ERR_INVALID_ARG, "scene is NULL");
+    DeviceGuard guard(S->device);
+    sput_status st = ensure_scratch(S);
+    if (st != SPUT_OK) return st;
+    return run_impl(S, opts, reinterpret_cast<cudaStream_t>(stream), T, stats, S->d_scratch);
+}
+
+sput_status sput_run_host(sput_scene* S, const sput_run_opts* opts, const sput_tallies* H, sput_run_stats* stats)
+{
+    if (!S || !opts || !H) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    if (H->records) return fail(SPUT_ERR_UNSUPPORTED, "records are device-only; use sput_run");
+    DeviceGuard guard(S->device);
+    sput_status st = ensure_scratch(S);
+    if (st != SPUT_OK) return st;
+    const TallySizes sz = tally_sizes(S);
+    size_t off[7], o = 0;
+    const size_t bytes[7] = {sz.counts, sz.energy, sz.score, sz.prim_counts, sz.timed_out, sz.hist_E, sz.hist_A};
+    for (int i = 0; i < 7; ++i) {
+        off[i] = o;
+        o = align_up(o + bytes[i], 256);
+    }
+    if (S->stage_bytes < o) {
+        if (S->d_stage) cudaFree(S->d_stage);
+        S->d_stage = nullptr;
+        S->stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&S->d_stage, o);
+        if (e != cudaSuccess) return fail(SPUT_ERR_NO_MEMORY, "cudaMalloc staging tallies");
+        S->stage_bytes = o;
+    }
+    if (!S->own_stream) CUDA_TRY(cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking));
+    unsigned char* base = reinterpret_cast<unsigned char*>(S->d_stage);
+    void* hp[7] = {H->counts, H->energy, H->score, H->prim_counts, H->timed_out, H->hist_E, H->hist_A};
+    sput_tallies D{};
+    void** dp[7] = {&D.counts, reinterpret_cast<void**>(&D.energy), reinterpret_cast<void**>(&D.score),
+                    reinterpret_cast<void**>(&D.prim_counts), reinterpret_cast<void**>(&D.timed_out),
+                    reinterpret_cast<void**>(&D.hist_E), reinterpret_cast<void**>(&D.hist_A)};
+    for (int i = 0; i < 7; ++i) *dp[i] = hp[i] ? base + off[i] : nullptr;
+    sput_run_opts o2 = *opts;
+    if (o2.accumulate) {
+        // accumulate into the caller's host values: upload them first
+        for (int i = 0; i < 7; ++i)
+            if (hp[i]) CUDA_TRY(cudaMemcpyAsync(base + off[i], hp[i], bytes[i], cudaMemcpyHostToDevice, S->own_stream));
+    }
+    sput_run_stats local{};
+    st = run_impl(S, &o2, S->own_stream, &D, stats ? stats : &local, S->d_scratch);
+    if (st != SPUT_OK) return st;
+    for (int i = 0; i < 7; ++i)
+        if (hp[i]) CUDA_TRY(cudaMemcpyAsync(hp[i], base + off[i], bytes[i], cudaMemcpyDeviceToHost, S->own_stream));
+    CUDA_TRY(cudaStreamSynchronize(S->own_stream));
+    return SPUT_OK;
+}
+
+void sput_scene_destroy(sput_scene* S)
+{
+    if (!S) return;
+    {
+        DeviceGuard guard(S->device);
+        if (S->d_blob) cudaFree(S->d_blob);
+        if (S->d_scratch) cudaFree(S->d_scratch);
+        if (S->d_stage) cudaFree(S->d_stage);
+        if (S->h_scratch) cudaFreeHost(S->h_scratch);
+        if (S->ev0) cudaEventDestroy(S->ev0);
+        if (S->ev1) cudaEventDestroy(S->ev1);
+        if (S->own_stream) cudaStreamDestroy(S->own_stream);
+    }
+    delete S;
+}
+
+sput_status sput_probe(sput_scene* S, int what, int idx, int n, const double* x, double* y)
+{
+    if (!S || !x || !y || n < 0) return fail(SPUT_ERR_INVALID_ARG, "NULL argument or negative n");
+    if (what < SPUT_PROBE_CHI || what > SPUT_PROBE_LAUNCH) return fail(SPUT_ERR_INVALID_ARG, "unknown probe");
+    if ((what == SPUT_PROBE_K || what == SPUT_PROBE_M) && (idx < 0 || idx >= (int)S->dpairs.size()))
+        return fail(SPUT_ERR_INVALID_ARG, "pair index out of range");
+    if (what == SPUT_PROBE_LAUNCH && (idx < 0 || idx >= (int)S->dinst.size()))
+        return fail(SPUT_ERR_INVALID_ARG, "instance index out of range");
+    if ((what == SPUT_PROBE_CHI || what == SPUT_PROBE_BMAX) && !S->bt)
+        return fail(SPUT_ERR_UNSUPPORTED, "no Moliere tables in a hard-sphere scene");
+    if (n == 0) return SPUT_OK;
+    DeviceGuard guard(S->device);
+    const size_t nx = (size_t)n * (what == SPUT_PROBE_CHI ? 2 : 1), ny = (size_t)n * (what == SPUT_PROBE_LAUNCH ? 7 : 1);
+    double *dx = nullptr, *dy = nullptr;
+    CUDA_TRY(cudaMalloc(&dx, nx * sizeof(double)));
+    cudaError_t e = cudaMalloc(&dy, ny * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, nx * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = (cudaError_t)probe_launch(S->base, what, idx, n, dx, dy, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(y, dy, ny * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    if (dy) cudaFree(dy);
+    if (e != cudaSuccess) return cuda_fail(e, "probe");
+    return SPUT_OK;
+}
+
+}  // extern "C"

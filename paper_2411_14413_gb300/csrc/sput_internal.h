@@ -1,0 +1,152 @@
+// sput_internal.h -- device-side scene layout shared by the host library and
+// the CUDA kernels of libsput.so (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "sput.h"
+
+namespace sput {
+
+// Scattering integral: Gauss-Mehler (Gauss-Chebyshev) quadrature with
+// kGMNodes nodes on [-1,1]; by symmetry kGMNodes/2 evaluations.
+constexpr int kGMNodes = 32;
+constexpr int kGMHalf = kGMNodes / 2;
+// Newton steps for the apsis from the head-on lower bound (converges to
+// < 2e-8 relative within 5 steps over the whole eps, b range; one spare).
+constexpr int kApsisIters = 6;
+
+// Moliere screening: Phi(x) = sum c_i exp(-d_i x) (Moliere 1947).
+constexpr float kMolC0 = 0.35f, kMolC1 = 0.55f, kMolC2 = 0.10f;
+constexpr float kMolD0 = 0.3f, kMolD1 = 1.2f, kMolD2 = 6.0f;
+
+// Rejection bound window: M(v) = max over g <= v + kMajorantSigmas * s of sigma(g) g.
+constexpr double kMajorantSigmas = 6.0;
+
+// Device status bits (sput_run_stats.device_status).
+enum : uint32_t {
+    kStatusNonFinite = 1u << 0,   // a particle state became NaN/Inf; the particle was retired as timed out
+    kStatusBadIndex = 1u << 1,    // a tally or table index fell outside its buffer; the write was skipped
+};
+
+// One primitive, 64 bytes; n = u x v precomputed.
+struct alignas(16) DevPrim {
+    float cx, cy, cz;
+    int kind;
+    float ux, uy, uz;
+    float p0;
+    float vx, vy, vz;
+    float p1;
+    float nx, ny, nz;
+    float p0sq;  // disc: inner radius^2; cylinder: radius^2
+};
+
+struct alignas(16) DevGeom {
+    int begin, count, substrate, pad;
+};
+
+struct alignas(16) DevCathode {
+    float c[3], n[3], e1[3], e2[3];
+    // racetrack: radial pdf ~ r exp(-z^2), z = (r - r0) k, k = 1/(sigma sqrt 2), on [0, R];
+    // CDF numerator F(r) = A (C - exp(-z^2)) + B (erf(z) + E0), FR = F(R)
+    float rt_r0, rt_R, rt_FR, rt_A;
+    float rt_B, rt_C, rt_E0, rt_k;
+    float coef[6];
+    float coef_norm;                       // sum c_i/(i+1)
+    int cos_general;                       // 0 = pure cosine (mu = sqrt(u))
+    int target;                            // local index of the target disc
+    int pair;                              // interaction pair (tables)
+    int rt_tab;                            // offset of this cathode's racetrack guess table
+    int pad0;
+    float v_per_sqrtE;                     // speed (km/s) = v_per_sqrtE * sqrt(E / eV)
+    float E_per_v2;                        // E (eV) = E_per_v2 * v^2
+    float pad1, pad2;
+};
+
+struct alignas(16) DevPair {
+    float kappa;        // eps = kappa * g^2 (g in km/s)
+    float ln_kappa;
+    float sigma_scale;  // sigma (A^2) = sigma_scale * (b_max/a)^2  (hard sphere: pi d^2)
+    float m1M;          // m1 / (m1 + m2)
+    float m2M;          // m2 / (m1 + m2)
+    int hard_sphere;
+    int K_off, M_off;   // float4 offsets of the <sigma g>(w) and M(w) tables
+    int n_w;            // intervals of the w tables
+    float w_inv_h;      // 1 / Delta w
+    float inv_s;        // 1 / s_gas, w = ln(1 + v / s_gas)
+    float pad;
+};
+
+struct alignas(16) DevInstance {
+    int geometry, cathode, pair;
+    uint32_t n;           // particles
+    float ng14;           // n_gas (mm^-3) * 1e-14: inverse mean free path = ng14 * K / v
+    float thompson_q;     // E_max / (E_max + U_s)
+    float U_s;
+    float pad;
+    unsigned long long ticket_begin;
+    unsigned long long pad2;
+};
+
+// Everything the transport kernel needs; passed by value (kernel parameter).
+struct Params {
+    // scene (device pointers)
+    const DevPrim* prims;
+    const DevGeom* geoms;
+    const DevCathode* cath;
+    const DevPair* pairs;
+    const DevInstance* inst;
+    const unsigned long long* prefix;  // n_inst + 1 ticket offsets
+    const float4* bm_tab;              // n_bm cubic pieces of b_max/a over ln eps
+    const float* xh_tab;               // n_bm + 1 head-on apsis values (linear)
+    const float4* w_tab;               // all pairs' K and M pieces
+    const float* rt_tab;               // racetrack guesses
+    int n_prims, n_geoms, n_pairs, n_inst;
+    int n_bm, n_w_total;
+    float bm_lo, bm_inv_h;
+    float box_lo[3], box_hi[3];
+    float s_gas;
+    int gas_thermal;
+    int max_attempts;
+    int max_prims;
+    long long max_collisions;
+    int rt_n;                          // racetrack guess nodes per cathode - 1
+    // grid
+    int nx, ny;
+    float half_u, half_v, cells_per_mm_u, cells_per_mm_v;
+    int n_ebins, n_abins;
+    float ebin_per_eV;
+    // tallies (caller-owned device memory, may be null)
+    void* counts;
+    double* energy;
+    double* score;
+    long long* prim_counts;
+    long long* timed_out;
+    long long* hist_E;
+    long long* hist_A;
+    sput_record* records;
+    // run
+    uint32_t key0, key1;
+    unsigned long long ticket_begin, ticket_end;
+    int chunk;
+    int smem_counters;                 // prim/timed-out counters privatised in shared memory
+    // scratch (library-owned device memory)
+    unsigned long long* ticket_counter;
+    unsigned long long* stats;         // [particles, landed, timed_out, flights, collisions, attempts]
+    unsigned int* status;
+    // Gauss-Mehler node constants per evaluation j: (u_j, 1/(1+u_j), u_j/(1-u_j^2), 1/u_j - 1)
+    float4 gm[kGMHalf];
+};
+
+constexpr int kNumStats = 6;
+
+// Launchers implemented in sput_transport.cu.
+int transport_configure(int max_dynamic_smem);
+int transport_launch(const Params& p, int count64, int blocks, int threads, size_t smem, void* stream);
+size_t transport_smem_bytes(const Params& p);
+int transport_max_blocks_per_sm(int count64, int threads, size_t smem);
+int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev, double* y_dev, void* stream);
+
+}  // namespace sput

@@ -1,0 +1,77 @@
+// sput_tables.h -- FP64 host construction of the interaction tables of
+// libsput.so (cross section, head-on apsis, collision rate, rejection bound,
+// racetrack guesses).  Internal to the library.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace sput {
+
+// Physical constants (CODATA 2018).
+constexpr double kAmuKg = 1.66053906660e-27;
+constexpr double kElemCharge = 1.602176634e-19;
+constexpr double kBoltzmannJ = 1.380649e-23;
+constexpr double kBoltzmannEV = 8.617333262e-5;
+constexpr double kBohrA = 0.529177210903;
+constexpr double kE2EVA = 14.3996454784;  // e^2/(4 pi eps0), eV*Angstrom
+constexpr double kPi = 3.14159265358979323846;
+// kinetic energy (eV) of 1 u at 1 km/s
+constexpr double kEnergyUnit = kAmuKg * 1.0e6 / kElemCharge;
+
+// b_max / a of the Moliere potential over ln(eps), piecewise cubic on a
+// uniform grid; each piece interpolates four exactly root-found values.
+struct BmaxTable {
+    double chi_min = 0.0;
+    double lo = -42.0, h = 0.05;
+    int n = 0;                       // pieces
+    std::vector<double> third;       // 3n+1 values at lo + h*j/3
+    std::vector<float4> cubic;       // per piece c0 + t(c1 + t(c2 + t c3)), t in [0,1]
+    std::vector<float> xh;           // head-on apsis at the n+1 nodes
+    double eval(double ln_eps) const;  // FP64 evaluation of the same pieces
+};
+
+// Cached per chi_min (thread-safe).
+const BmaxTable& bmax_table(double chi_min);
+
+// Reduced-unit Moliere scattering: closest approach and CM deflection (FP64).
+double head_on_apsis64(double eps);
+double apsis64(double eps, double beta);
+double chi_moliere64(double eps, double beta);
+
+struct PairPhys {
+    double Z1, Z2, m1, m2;
+    double a;          // Firsov screening length, Angstrom
+    double zze2;       // Z1 Z2 e^2, eV*Angstrom
+    double kappa;      // eps = kappa g^2
+    int hard_sphere;
+    double hs_d;       // Angstrom
+    double chi_min;
+};
+
+PairPhys make_pair(double Z1, double m1, double Z2, double m2, int hard_sphere, double hs_d, double chi_min);
+
+// sigma(g) in Angstrom^2 (g in km/s)
+double sigma64(const PairPhys& pp, const BmaxTable* bt, double g);
+
+// Tables in w = ln(1 + v/s) with pieces of width h_w up to w(v_top):
+// K(v) = <sigma(g) g> over the Maxwellian gas (gas at rest: sigma(v) = K(v)/v) and the
+// rejection bound M(v) = max_{g <= v + 6 s} sigma(g) g.
+void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v_top,
+                    double h_w, std::vector<float4>& K, std::vector<float4>& M, int& n_w);
+
+// FP64 host values used by tests through the probe entry point.
+double K64(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v);
+double M64(const PairPhys& pp, const BmaxTable* bt, double s_gas, double v, int monotone);
+int h_monotone(const PairPhys& pp, const BmaxTable* bt, double g_top);
+
+// Racetrack inverse-CDF guesses at u = (j/n)^2, j = 0..n.
+void racetrack_guess(double r0, double sigma, double R, int n, float* out);
+double racetrack_F64(double r0, double sigma, double r);
+
+// Cubic through f(0), f(1/3), f(2/3), f(1) on t in [0,1].
+float4 cubic_from_thirds(double f0, double f1, double f2, double f3);
+
+}  // namespace sput

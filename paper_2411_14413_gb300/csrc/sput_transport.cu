@@ -1,0 +1,715 @@
+// sput_transport.cu -- persistent Monte Carlo transport kernel for sm_103a.
+//
+// One thread carries one sputtered atom at a time; a warp refills its dead
+// lanes from a warp-private pool of tickets that it takes in chunks from one
+// global counter, so every lane runs exactly one free flight per loop
+// iteration (Sec. "The SIMTRA model": launch, free flight, surface test,
+// binary collision, repeated until the atom lands).  Geometry and the
+// interaction tables are staged in shared memory; the per-collision
+// scattering angle is computed from the classical deflection integral by
+// Gauss-Mehler quadrature in FP32.  Counts are integer atomics (bit-exact,
+// order independent); energy and score sums are FP64 atomics.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cstdint>
+
+#include "sput_internal.h"
+
+namespace sput {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ----------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
+// multiplies with the published multipliers and Weyl key increments.
+__device__ __forceinline__ uint4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                                        uint32_t c3)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// RN in ]0,1]: ((x >> 8) + 1) 2^-24, exact in FP32
+__device__ __forceinline__ float rn(uint32_t x) { return (float)((x >> 8) + 1u) * 5.9604644775390625e-8f; }
+
+// ------------------------------------------------------------- tables
+__device__ __forceinline__ float cubic_eval(const float4* tab, int n, float x)
+{
+    // x in piece units; clamped to [0, n]
+    x = fminf(fmaxf(x, 0.0f), (float)n);
+    int i = min((int)x, n - 1);
+    float t = x - (float)i;
+    float4 c = tab[i];
+    return fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
+}
+
+struct TableView {
+    const float4* bm;
+    const float* xh;
+    const float4* w;
+    const DevPair* pairs;
+    int n_bm;
+    float bm_lo, bm_inv_h;
+};
+
+__device__ __forceinline__ float bmax_eval(const TableView& T, float ln_eps)
+{
+    return cubic_eval(T.bm, T.n_bm, (ln_eps - T.bm_lo) * T.bm_inv_h);
+}
+
+__device__ __forceinline__ float xh_eval(const TableView& T, float ln_eps)
+{
+    float x = fminf(fmaxf((ln_eps - T.bm_lo) * T.bm_inv_h, 0.0f), (float)T.n_bm);
+    int i = min((int)x, T.n_bm - 1);
+    float t = x - (float)i;
+    return fmaf(t, T.xh[i + 1] - T.xh[i], T.xh[i]);
+}
+
+// K(v) or M(v) of a pair: cubic pieces in w = ln(1 + v/s)
+__device__ __forceinline__ float wtab_eval(const TableView& T, const DevPair& pr, int off, float v)
+{
+    float w = log1pf(v * pr.inv_s);
+    return cubic_eval(T.w + off, pr.n_w, w * pr.w_inv_h);
+}
+
+// sigma(g) g in A^2 km/s
+__device__ __forceinline__ float h_of_g(const TableView& T, const DevPair& pr, float g, float g2)
+{
+    if (pr.hard_sphere) return pr.sigma_scale * g;
+    float b = bmax_eval(T, __logf(pr.kappa * g2));
+    return pr.sigma_scale * b * b * g;
+}
+
+// 1 - exp(-y) without cancellation for small y
+__device__ __forceinline__ float one_minus_exp_neg(float y)
+{
+    if (y < 0.5f) {
+        float s = 1.0f - y * (1.0f / 10.0f);
+        s = 1.0f - y * (1.0f / 9.0f) * s;
+        s = 1.0f - y * (1.0f / 8.0f) * s;
+        s = 1.0f - y * (1.0f / 7.0f) * s;
+        s = 1.0f - y * (1.0f / 6.0f) * s;
+        s = 1.0f - y * (1.0f / 5.0f) * s;
+        s = 1.0f - y * (1.0f / 4.0f) * s;
+        s = 1.0f - y * (1.0f / 3.0f) * s;
+        s = 1.0f - y * (1.0f / 2.0f) * s;
+        return y * s;
+    }
+    return 1.0f - expf(-y);
+}
+
+// CM deflection for the Moliere potential in reduced units (eps, beta):
+// apsis by Newton from the head-on lower bound max(beta, x_h), then the
+// Gauss-Mehler sum chi = (2 pi / N) sum_j D_j / (S_j (S_j + beta/x0)).
+__device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
+{
+    const float ie = 1.0f / eps;
+    const float b2 = beta * beta;
+    float x = fmaxf(beta, xh);
+#pragma unroll
+    for (int it = 0; it < kApsisIters; ++it) {
+        float e0 = kMolC0 * expf(-kMolD0 * x), e1 = kMolC1 * expf(-kMolD1 * x), e2 = kMolC2 * expf(-kMolD2 * x);
+        float ph = e0 + e1 + e2;
+        float dph = -(kMolD0 * e0 + kMolD1 * e1 + kMolD2 * e2);
+        float ix = 1.0f / x;
+        float ix2 = ix * ix;
+        float g = 1.0f - b2 * ix2 - ph * ix * ie;
+        float gp = 2.0f * b2 * ix2 * ix - (dph * x - ph) * ix2 * ie;
+        x -= g / gp;
+    }
+    const float x0 = x;
+    const float bt = beta / x0;
+    const float bt2 = bt * bt;
+    const float iex = ie / x0;
+    const float p0 = kMolC0 * expf(-kMolD0 * x0) * iex;
+    const float p1 = kMolC1 * expf(-kMolD1 * x0) * iex;
+    const float p2 = kMolC2 * expf(-kMolD2 * x0) * iex;
+    const float y0 = kMolD0 * x0, y1 = kMolD1 * x0, y2 = kMolD2 * x0;
+    float s = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < kGMHalf; ++j) {
+        const float4 nd = gm[j];  // (u, 1/(1+u), u/(1-u^2), 1/u - 1)
+        float D = p0 * fmaf(nd.z, one_minus_exp_neg(y0 * nd.w), nd.y);
+        D = fmaf(p1, fmaf(nd.z, one_minus_exp_neg(y1 * nd.w), nd.y), D);
+        D = fmaf(p2, fmaf(nd.z, one_minus_exp_neg(y2 * nd.w), nd.y), D);
+        float S = sqrtf(bt2 + D);
+        s += D / (S * (S + bt));
+    }
+    return s * (6.283185307179586f / (float)kGMNodes);
+}
+
+// orthonormal pair perpendicular to unit n (Duff et al., JCGT 6(1), 2017)
+__device__ __forceinline__ void onb(float nx, float ny, float nz, float3& b1, float3& b2)
+{
+    float sgn = copysignf(1.0f, nz);
+    float a = -1.0f / (sgn + nz);
+    float b = nx * ny * a;
+    b1 = make_float3(1.0f + sgn * nx * nx * a, sgn * b, -sgn * nx);
+    b2 = make_float3(b, sgn + ny * ny * a, -ny);
+}
+
+// ------------------------------------------------------------- launch
+struct Lane {
+    float px, py, pz, dx, dy, dz, speed, score;
+    uint32_t pid, inst, k, ncoll;
+    int gbegin, gcount, gsub, target, pair;
+    float ng14, E_per_v2;
+    unsigned long long ticket;
+};
+
+__device__ float racetrack_r(const DevCathode& C, const float* rt_tab, int rt_n, float u)
+{
+    // table guess in sqrt(u), then Newton on the closed-form CDF numerator
+    float x = sqrtf(u) * (float)rt_n;
+    int j = min((int)x, rt_n - 1);
+    float f = x - (float)j;
+    const float* g = rt_tab + C.rt_tab;
+    float r = fmaf(f, g[j + 1] - g[j], g[j]);
+    const float T = u * C.rt_FR;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        float z = (r - C.rt_r0) * C.rt_k;
+        float e = expf(-z * z);
+        float F = fmaf(C.rt_A, C.rt_C - e, C.rt_B * (erff(z) + C.rt_E0));
+        float pdf = r * e;
+        if (pdf > 1e-30f) r -= (F - T) / pdf;
+        r = fminf(fmaxf(r, 0.0f), C.rt_R);
+    }
+    return r;
+}
+
+__device__ float cosine_sum_mu(const DevCathode& C, float u)
+{
+    if (!C.cos_general) return sqrtf(u);
+    // bisection on the polynomial CDF sum c_i mu^{i+1}/(i+1)
+    const float tgt = u * C.coef_norm;
+    float lo = 0.0f, hi = 1.0f;
+    for (int it = 0; it < 26; ++it) {
+        float m = 0.5f * (lo + hi);
+        float F = C.coef[5] * (1.0f / 6.0f);
+        F = fmaf(F, m, C.coef[4] * (1.0f / 5.0f));
+        F = fmaf(F, m, C.coef[3] * (1.0f / 4.0f));
+        F = fmaf(F, m, C.coef[2] * (1.0f / 3.0f));
+        F = fmaf(F, m, C.coef[1] * (1.0f / 2.0f));
+        F = fmaf(F, m, C.coef[0]);
+        F *= m;
+        if (F < tgt) lo = m;
+        else hi = m;
+    }
+    return 0.5f * (lo + hi);
+}
+
+__device__ void launch_state(const Params& P, const float* rt_tab, uint32_t inst, uint32_t pid, float& px,
+                             float& py, float& pz, float& dx, float& dy, float& dz, float& E)
+{
+    const DevInstance& I = P.inst[inst];
+    const DevCathode& C = P.cath[I.cathode];
+    const uint4 w0 = philox(P.key0, P.key1, pid, inst, 0u, 0u);
+    const uint4 w1 = philox(P.key0, P.key1, pid, inst, 0u, 1u);
+    const float r = racetrack_r(C, rt_tab, P.rt_n, rn(w0.x));
+    float sa, ca;
+    sincospif(2.0f * rn(w0.y), &sa, &ca);
+    const float s = sqrtf(rn(w0.z)) * I.thompson_q;
+    E = I.U_s * s / (1.0f - s);
+    const float mu = cosine_sum_mu(C, rn(w0.w));
+    float sp, cp;
+    sincospif(2.0f * rn(w1.x), &sp, &cp);
+    const float st = sqrtf((1.0f - mu) * (1.0f + mu));
+    const float rc = r * ca, rs = r * sa, tc = st * cp, ts = st * sp;
+    px = C.c[0] + rc * C.e1[0] + rs * C.e2[0];
+    py = C.c[1] + rc * C.e1[1] + rs * C.e2[1];
+    pz = C.c[2] + rc * C.e1[2] + rs * C.e2[2];
+    dx = tc * C.e1[0] + ts * C.e2[0] + mu * C.n[0];
+    dy = tc * C.e1[1] + ts * C.e2[1] + mu * C.n[1];
+    dz = tc * C.e1[2] + ts * C.e2[2] + mu * C.n[2];
+}
+
+// ------------------------------------------------------------- geometry
+__device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, float px, float py, float pz, float dx,
+                                          float dy, float dz)
+{
+    float t = CUDART_INF_F;
+    if (Q.kind == SPUT_PRIM_BOX) {
+        float tx = dx > 0.0f ? (P.box_hi[0] - px) / dx : (dx < 0.0f ? (P.box_lo[0] - px) / dx : CUDART_INF_F);
+        float ty = dy > 0.0f ? (P.box_hi[1] - py) / dy : (dy < 0.0f ? (P.box_lo[1] - py) / dy : CUDART_INF_F);
+        float tz = dz > 0.0f ? (P.box_hi[2] - pz) / dz : (dz < 0.0f ? (P.box_lo[2] - pz) / dz : CUDART_INF_F);
+        t = fmaxf(fminf(tx, fminf(ty, tz)), 0.0f);
+    } else if (Q.kind == SPUT_PRIM_CYLINDER) {
+        const float wx = px - Q.cx, wy = py - Q.cy, wz = pz - Q.cz;
+        const float wa = wx * Q.ux + wy * Q.uy + wz * Q.uz;
+        const float da = dx * Q.ux + dy * Q.uy + dz * Q.uz;
+        const float wpx = wx - wa * Q.ux, wpy = wy - wa * Q.uy, wpz = wz - wa * Q.uz;
+        const float dpx = dx - da * Q.ux, dpy = dy - da * Q.uy, dpz = dz - da * Q.uz;
+        const float A = dpx * dpx + dpy * dpy + dpz * dpz;
+        const float B = 2.0f * (wpx * dpx + wpy * dpy + wpz * dpz);
+        const float Cc = wpx * wpx + wpy * wpy + wpz * wpz - Q.p0sq;
+        const float disc = B * B - 4.0f * A * Cc;
+        if (A > 0.0f && disc >= 0.0f) {
+            const float sq = sqrtf(disc);
+            const float q = -0.5f * (B + copysignf(sq, B));
+            float r1 = q / A, r2 = q != 0.0f ? Cc / q : r1;
+            const float tlo = fminf(r1, r2), thi = fmaxf(r1, r2);
+            if (tlo > 0.0f && fabsf(fmaf(tlo, da, wa)) <= Q.p1) t = tlo;
+            else if (thi > 0.0f && fabsf(fmaf(thi, da, wa)) <= Q.p1) t = thi;
+        }
+    } else {
+        const float den = dx * Q.nx + dy * Q.ny + dz * Q.nz;
+        if (den != 0.0f) {
+            const float num = (Q.cx - px) * Q.nx + (Q.cy - py) * Q.ny + (Q.cz - pz) * Q.nz;
+            const float tt = num / den;
+            if (tt > 0.0f) {
+                const float qx = fmaf(tt, dx, px) - Q.cx, qy = fmaf(tt, dy, py) - Q.cy, qz = fmaf(tt, dz, pz) - Q.cz;
+                const float a1 = qx * Q.ux + qy * Q.uy + qz * Q.uz;
+                const float a2 = qx * Q.vx + qy * Q.vy + qz * Q.vz;
+                bool in;
+                if (Q.kind == SPUT_PRIM_RECT) in = fabsf(a1) <= Q.p0 && fabsf(a2) <= Q.p1;
+                else {
+                    const float r2 = a1 * a1 + a2 * a2;
+                    in = r2 >= Q.p0sq && r2 <= Q.p1 * Q.p1;
+                }
+                if (in) t = tt;
+            }
+        }
+    }
+    return t;
+}
+
+// ------------------------------------------------------------- kernel
+struct SmemLayout {
+    size_t prims, geoms, pairs, bm, w, prefix, xh, counters, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline SmemLayout smem_layout(const Params& p)
+{
+    SmemLayout L;
+    size_t o = 0;
+    L.prims = o;
+    o = align16(o + sizeof(DevPrim) * p.n_prims);
+    L.geoms = o;
+    o = align16(o + sizeof(DevGeom) * p.n_geoms);
+    L.pairs = o;
+    o = align16(o + sizeof(DevPair) * p.n_pairs);
+    L.bm = o;
+    o = align16(o + sizeof(float4) * p.n_bm);
+    L.w = o;
+    o = align16(o + sizeof(float4) * p.n_w_total);
+    L.prefix = o;
+    o = align16(o + sizeof(unsigned long long) * (p.n_inst + 1));
+    L.xh = o;
+    o = align16(o + sizeof(float) * (p.n_bm + 1));
+    L.counters = o;
+    o = align16(o + (p.smem_counters ? sizeof(unsigned int) * (size_t)p.n_inst * (p.max_prims + 1) : 0));
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
+{
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (size_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
+    const unsigned char* sb = reinterpret_cast<const unsigned char*>(src);
+    unsigned char* db = reinterpret_cast<unsigned char*>(dst);
+    for (size_t i = (bytes / 16) * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
+}
+
+template <bool kCount64>
+__global__ void __launch_bounds__(256) transport_kernel(const Params P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(P);
+    DevPrim* s_prims = reinterpret_cast<DevPrim*>(smem + L.prims);
+    DevGeom* s_geoms = reinterpret_cast<DevGeom*>(smem + L.geoms);
+    DevPair* s_pairs = reinterpret_cast<DevPair*>(smem + L.pairs);
+    float4* s_bm = reinterpret_cast<float4*>(smem + L.bm);
+    float4* s_w = reinterpret_cast<float4*>(smem + L.w);
+    unsigned long long* s_prefix = reinterpret_cast<unsigned long long*>(smem + L.prefix);
+    float* s_xh = reinterpret_cast<float*>(smem + L.xh);
+    unsigned int* s_cnt = reinterpret_cast<unsigned int*>(smem + L.counters);
+
+    copy16(s_prims, P.prims, sizeof(DevPrim) * P.n_prims);
+    copy16(s_geoms, P.geoms, sizeof(DevGeom) * P.n_geoms);
+    copy16(s_pairs, P.pairs, sizeof(DevPair) * P.n_pairs);
+    copy16(s_bm, P.bm_tab, sizeof(float4) * P.n_bm);
+    copy16(s_w, P.w_tab, sizeof(float4) * P.n_w_total);
+    copy16(s_prefix, P.prefix, sizeof(unsigned long long) * (P.n_inst + 1));
+    copy16(s_xh, P.xh_tab, sizeof(float) * (P.n_bm + 1));
+    const int n_cnt = P.smem_counters ? P.n_inst * (P.max_prims + 1) : 0;
+    for (int i = threadIdx.x; i < n_cnt; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+
+    TableView T;
+    T.bm = s_bm;
+    T.xh = s_xh;
+    T.w = s_w;
+    T.pairs = s_pairs;
+    T.n_bm = P.n_bm;
+    T.bm_lo = P.bm_lo;
+    T.bm_inv_h = P.bm_inv_h;
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lane_lt = (1u << lane) - 1u;
+    const int ncell = P.nx * P.ny;
+
+    Lane S;
+    S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = 0.0f;
+    S.pid = S.inst = S.k = S.ncoll = 0u;
+    S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
+    S.ng14 = S.E_per_v2 = 0.0f;
+    S.ticket = 0ull;
+    bool alive = false;
+
+    uint32_t c_particles = 0, c_landed = 0, c_timed = 0, c_flights = 0, c_coll = 0, c_att = 0;
+    unsigned long long pool_next = 0ull, pool_end = 0ull;
+    bool exhausted = false;
+
+    for (;;) {
+        // ---------------------------------------------------- refill (warp-uniform)
+        const unsigned need = __ballot_sync(kFull, !alive);
+        if (need) {
+            const unsigned n = __popc(need);
+            const unsigned rank = __popc(need & lane_lt);
+            const unsigned long long avail = pool_end - pool_next;
+            unsigned long long t = ~0ull;
+            if (!alive && rank < avail) t = pool_next + rank;
+            if (n > avail && !exhausted) {
+                const unsigned long long want = n - avail;
+                const unsigned long long grab = want > (unsigned long long)P.chunk ? want : (unsigned long long)P.chunk;
+                unsigned long long base = 0ull;
+                if (lane == 0) base = atomicAdd(P.ticket_counter, grab);
+                base = __shfl_sync(kFull, base, 0) + P.ticket_begin;
+                if (!alive && rank >= avail && base + (rank - avail) < P.ticket_end) t = base + (rank - avail);
+                unsigned long long ne = base + grab < P.ticket_end ? base + grab : P.ticket_end;
+                unsigned long long nn = base + want < ne ? base + want : ne;
+                pool_next = nn;
+                pool_end = ne;
+                if (base + grab >= P.ticket_end) exhausted = true;
+            } else {
+                pool_next += (n < avail ? n : avail);
+            }
+            if (t != ~0ull) {
+                // ticket -> (instance, particle id) by binary search over the instance prefix
+                int lo = 0, hi = P.n_inst;
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (s_prefix[mid] <= t) lo = mid;
+                    else hi = mid;
+                }
+                const DevInstance& I = P.inst[lo];
+                const DevGeom G = s_geoms[I.geometry];
+                const DevCathode& C = P.cath[I.cathode];
+                S.inst = (uint32_t)lo;
+                S.pid = (uint32_t)(t - s_prefix[lo]);
+                S.ticket = t;
+                S.gbegin = G.begin;
+                S.gcount = G.count;
+                S.gsub = G.substrate;
+                S.target = C.target;
+                S.pair = I.pair;
+                S.ng14 = I.ng14;
+                S.E_per_v2 = C.E_per_v2;
+                float E;
+                launch_state(P, P.rt_tab, S.inst, S.pid, S.px, S.py, S.pz, S.dx, S.dy, S.dz, E);
+                S.speed = C.v_per_sqrtE * sqrtf(E);
+                S.k = 0u;
+                S.ncoll = 0u;
+                S.score = 0.0f;
+                alive = true;
+            }
+        }
+        if (!__any_sync(kFull, alive)) break;
+        if (!alive) continue;
+
+        // ---------------------------------------------------- free flight
+        S.k += 1u;
+        ++c_flights;
+        const uint4 w = philox(P.key0, P.key1, S.pid, S.inst, S.k, 0u);
+        const DevPair pr = s_pairs[S.pair];
+        // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
+        const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
+        const float inv_lam = P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv;
+        const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
+
+        // ---------------------------------------------------- surface test
+        float tb = CUDART_INF_F;
+        int hb = -1;
+        const int excl = S.k == 1u ? S.target : -1;
+        for (int li = 0; li < S.gcount; ++li) {
+            if (li == excl) continue;
+            const float t = hit_prim(s_prims[S.gbegin + li], P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
+            if (t < tb) {
+                tb = t;
+                hb = li;
+            }
+        }
+
+        if (hb >= 0 && tb <= ell) {
+            // ------------------------------------------------ landing
+            S.score -= tb * inv_lam;
+            const float E = S.E_per_v2 * S.speed * S.speed;
+            int cell = -1;
+            float cosang = 0.0f;
+            if (hb == S.gsub) {
+                const DevPrim& Q = s_prims[S.gbegin + hb];
+                const float dn = S.dx * Q.nx + S.dy * Q.ny + S.dz * Q.nz;
+                if (dn < 0.0f) {
+                    const float qx = fmaf(tb, S.dx, S.px) - Q.cx, qy = fmaf(tb, S.dy, S.py) - Q.cy,
+                                qz = fmaf(tb, S.dz, S.pz) - Q.cz;
+                    const float a1 = qx * Q.ux + qy * Q.uy + qz * Q.uz;
+                    const float a2 = qx * Q.vx + qy * Q.vy + qz * Q.vz;
+                    const float fx = (a1 + P.half_u) * P.cells_per_mm_u;
+                    const float fy = (a2 + P.half_v) * P.cells_per_mm_v;
+                    if (fx >= 0.0f && fy >= 0.0f && fx <= (float)P.nx && fy <= (float)P.ny) {
+                        const int ix = min((int)fx, P.nx - 1), iy = min((int)fy, P.ny - 1);
+                        cell = iy * P.nx + ix;
+                    }
+                    cosang = -dn;
+                }
+            }
+            if (cell >= 0) {
+                const size_t ci = (size_t)S.inst * ncell + cell;
+                if (P.counts) {
+                    if (kCount64) atomicAdd(reinterpret_cast<unsigned long long*>(P.counts) + ci, 1ull);
+                    else atomicAdd(reinterpret_cast<unsigned int*>(P.counts) + ci, 1u);
+                }
+                if (P.energy) atomicAdd(P.energy + ci, (double)E);
+                if (P.score) atomicAdd(P.score + ci, (double)S.score);
+                if (P.hist_E) {
+                    int b = min(max((int)(E * P.ebin_per_eV), 0), P.n_ebins - 1);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(P.hist_E) + (size_t)S.inst * P.n_ebins + b, 1ull);
+                }
+                if (P.hist_A) {
+                    const float th = acosf(fminf(cosang, 1.0f)) * (57.29577951308232f / 90.0f);
+                    int b = min(max((int)(th * (float)P.n_abins), 0), P.n_abins - 1);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(P.hist_A) + (size_t)S.inst * P.n_abins + b, 1ull);
+                }
+            }
+            if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + hb], 1u);
+            else if (P.prim_counts)
+                atomicAdd(reinterpret_cast<unsigned long long*>(P.prim_counts) + (size_t)S.inst * P.max_prims + hb, 1ull);
+            if (P.records) {
+                sput_record rec;
+                rec.prim = hb;
+                rec.cell = cell;
+                rec.energy = E;
+                rec.cos_angle = cosang;
+                rec.n_collisions = S.ncoll;
+                rec.score = S.score;
+                P.records[S.ticket - P.ticket_begin] = rec;
+            }
+            ++c_landed;
+            ++c_particles;
+            alive = false;
+            continue;
+        }
+
+        // ---------------------------------------------------- move, then collide
+        S.px = fmaf(ell, S.dx, S.px);
+        S.py = fmaf(ell, S.dy, S.py);
+        S.pz = fmaf(ell, S.dz, S.pz);
+        S.score += 1.0f - ell * inv_lam;
+        if ((long long)S.k > P.max_collisions || !isfinite(S.px + S.py + S.pz + S.speed)) {
+            if (!isfinite(S.px + S.py + S.pz + S.speed)) atomicOr(P.status, kStatusNonFinite);
+            if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + P.max_prims], 1u);
+            else if (P.timed_out) atomicAdd(reinterpret_cast<unsigned long long*>(P.timed_out) + S.inst, 1ull);
+            if (P.records) {
+                sput_record rec;
+                rec.prim = -1;
+                rec.cell = -1;
+                rec.energy = S.E_per_v2 * S.speed * S.speed;
+                rec.cos_angle = 0.0f;
+                rec.n_collisions = S.ncoll;
+                rec.score = S.score;
+                P.records[S.ticket - P.ticket_begin] = rec;
+            }
+            ++c_timed;
+            ++c_particles;
+            alive = false;
+            continue;
+        }
+
+        const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
+        float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
+        if (P.gas_thermal) {
+            // gas partner: Maxwellian weighted by sigma(g) g, rejection against M(v)
+            const float M = wtab_eval(T, pr, pr.M_off, S.speed);
+            uint4 wa = make_uint4(0u, 0u, 0u, 0u);
+            for (int a = 0; a < P.max_attempts; ++a) {
+                const uint4 wn = philox(P.key0, P.key1, S.pid, S.inst, S.k, 1u + (uint32_t)a);
+                const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
+                const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
+                float s1, c1;
+                sincospif(2.0f * rn(wn.y), &s1, &c1);
+                const float c3 = cospif(2.0f * rn(wn.w));
+                Vx = P.s_gas * R0 * c1;
+                Vy = P.s_gas * R0 * s1;
+                Vz = P.s_gas * R1 * c3;
+                float ua;
+                if (a == 0) ua = rn(w.w);
+                else {
+                    const int q = (a - 1) & 3;
+                    if (q == 0) wa = philox(P.key0, P.key1, S.pid, S.inst, S.k, 1u + (uint32_t)P.max_attempts + (uint32_t)((a - 1) >> 2));
+                    ua = rn(q == 0 ? wa.x : (q == 1 ? wa.y : (q == 2 ? wa.z : wa.w)));
+                }
+                const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
+                const float g2 = gx * gx + gy * gy + gz * gz;
+                ++c_att;
+                if (ua * M <= h_of_g(T, pr, sqrtf(g2), g2)) break;
+            }
+        }
+        // binary collision in the CM frame: rotate g = v - V by (chi, psi), |g| kept
+        const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
+        const float g2 = gx * gx + gy * gy + gz * gz;
+        if (g2 > 0.0f) {
+            const float g = sqrtf(g2);
+            const float ig = 1.0f / g;
+            const float hx = gx * ig, hy = gy * ig, hz = gz * ig;
+            float chi;
+            if (pr.hard_sphere) {
+                chi = 2.0f * acosf(sqrtf(rn(w.y)));
+            } else {
+                const float eps = pr.kappa * g2;
+                const float le = logf(eps);
+                const float beta = bmax_eval(T, le) * sqrtf(rn(w.y));
+                chi = chi_moliere(eps, beta, xh_eval(T, le), P.gm);
+            }
+            float sc, cc, sp, cp;
+            sincosf(chi, &sc, &cc);
+            sincospif(2.0f * rn(w.z), &sp, &cp);
+            float3 b1, b2;
+            onb(hx, hy, hz, b1, b2);
+            const float gpx = g * (cc * hx + sc * (cp * b1.x + sp * b2.x));
+            const float gpy = g * (cc * hy + sc * (cp * b1.y + sp * b2.y));
+            const float gpz = g * (cc * hz + sc * (cp * b1.z + sp * b2.z));
+            const float nvx = pr.m1M * vx + pr.m2M * Vx + pr.m2M * gpx;
+            const float nvy = pr.m1M * vy + pr.m2M * Vy + pr.m2M * gpy;
+            const float nvz = pr.m1M * vz + pr.m2M * Vz + pr.m2M * gpz;
+            const float sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
+            S.speed = sqrtf(sp2);
+            const float is = 1.0f / S.speed;
+            S.dx = nvx * is;
+            S.dy = nvy * is;
+            S.dz = nvz * is;
+        }
+        ++S.ncoll;
+        ++c_coll;
+    }
+
+    // ---------------------------------------------------- flush counters
+    unsigned long long v[kNumStats] = {c_particles, c_landed, c_timed, c_flights, c_coll, c_att};
+#pragma unroll
+    for (int i = 0; i < kNumStats; ++i) {
+        unsigned long long x = v[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if (lane == 0 && x) atomicAdd(P.stats + i, x);
+    }
+    if (P.smem_counters) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_cnt; i += blockDim.x) {
+            const unsigned int c = s_cnt[i];
+            if (!c) continue;
+            const int inst = i / (P.max_prims + 1), li = i % (P.max_prims + 1);
+            if (li < P.max_prims) {
+                if (P.prim_counts)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(P.prim_counts) + (size_t)inst * P.max_prims + li,
+                              (unsigned long long)c);
+            } else if (P.timed_out) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(P.timed_out) + inst, (unsigned long long)c);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- probes
+__global__ void probe_kernel(const Params P, int what, int idx, int n, const double* x, double* y)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    TableView T;
+    T.bm = P.bm_tab;
+    T.xh = P.xh_tab;
+    T.w = P.w_tab;
+    T.pairs = P.pairs;
+    T.n_bm = P.n_bm;
+    T.bm_lo = P.bm_lo;
+    T.bm_inv_h = P.bm_inv_h;
+    if (what == SPUT_PROBE_CHI) {
+        const float eps = (float)x[2 * i], beta = (float)x[2 * i + 1];
+        const float le = logf(eps);
+        y[i] = chi_moliere(eps, beta, xh_eval(T, le), P.gm);
+    } else if (what == SPUT_PROBE_BMAX) {
+        y[i] = bmax_eval(T, logf((float)x[i]));
+    } else if (what == SPUT_PROBE_K || what == SPUT_PROBE_M) {
+        const DevPair pr = P.pairs[idx];
+        const float v = (float)x[i];
+        float val = wtab_eval(T, pr, what == SPUT_PROBE_K ? pr.K_off : pr.M_off, v);
+        if (what == SPUT_PROBE_K && !P.gas_thermal) val *= v;  // the table holds sigma(v) = K/v
+        y[i] = val;
+    } else if (what == SPUT_PROBE_LAUNCH) {
+        float px, py, pz, dx, dy, dz, E;
+        launch_state(P, P.rt_tab, (uint32_t)idx, (uint32_t)x[i], px, py, pz, dx, dy, dz, E);
+        double* o = y + 7 * (size_t)i;
+        o[0] = px;
+        o[1] = py;
+        o[2] = pz;
+        o[3] = dx;
+        o[4] = dy;
+        o[5] = dz;
+        o[6] = E;
+    }
+}
+
+}  // namespace
+
+size_t transport_smem_bytes(const Params& p) { return smem_layout(p).total; }
+
+int transport_max_blocks_per_sm(int count64, int threads, size_t smem)
+{
+    int nb = 0;
+    cudaError_t e;
+    if (count64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<true>, threads, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<false>, threads, smem);
+    return e == cudaSuccess ? nb : 0;
+}
+
+int transport_configure(int max_dynamic_smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(transport_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(transport_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
+    return (int)e;
+}
+
+int transport_launch(const Params& p, int count64, int blocks, int threads, size_t smem, void* stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (count64) transport_kernel<true><<<blocks, threads, smem, s>>>(p);
+    else transport_kernel<false><<<blocks, threads, smem, s>>>(p);
+    return (int)cudaGetLastError();
+}
+
+int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev, double* y_dev, void* stream)
+{
+    if (n <= 0) return 0;
+    probe_kernel<<<(n + 127) / 128, 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p, what, idx, n, x_dev, y_dev);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace sput
