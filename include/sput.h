@@ -281,13 +281,20 @@ void sput_scene_destroy(sput_scene* scene);
  *   SPUT_PROBE_K        x[n]  = speed (km/s), pair p       -> y[n] = <sigma g> (A^2 km/s)
  *   SPUT_PROBE_M        x[n]  = speed (km/s), pair p       -> y[n] = M(v) (A^2 km/s)
  *   SPUT_PROBE_LAUNCH   x[n]  = particle id, instance p    -> y[7n] = (x,y,z, dx,dy,dz, E)
- * p is the pair index (one per cathode) or the instance index. */
+ *   SPUT_PROBE_TRACE    x[n]  = particle id, instance p    -> y[640n]: 64 rows of
+ *       (x,y,z, dx,dy,dz, speed, status, a, t): row 0 the launch (status -1), row r the
+ *       state after flight r (status 0 collided: position = collision point, direction and
+ *       speed after the collision, a = partner attempts, t = flight length; 1 landed:
+ *       position = hit point, a = primitive, t = hit distance; 2 timed out; -2 unused)
+ * p is the pair index (one per distinct cathode element) or the instance index.
+ * This call allocates and frees temporary device buffers. */
 typedef enum sput_probe_kind {
     SPUT_PROBE_CHI = 0,
     SPUT_PROBE_BMAX = 1,
     SPUT_PROBE_K = 2,
     SPUT_PROBE_M = 3,
-    SPUT_PROBE_LAUNCH = 4
+    SPUT_PROBE_LAUNCH = 4,
+    SPUT_PROBE_TRACE = 5
 } sput_probe_kind;
 
 sput_status sput_probe(sput_scene* scene, int what, int p, int n, const double* x, double* y);

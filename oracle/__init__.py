@@ -100,6 +100,8 @@ def lib():
             L.or_partner.argtypes = [p, u64, i, u64, C.c_uint32, p, p]
             L.or_thermalize.restype = None
             L.or_thermalize.argtypes = [p, u64, i, u64, d, i, p]
+            L.or_trace.restype = None
+            L.or_trace.argtypes = [p, u64, i, u64, i, p]
             L.or_launch.restype = None
             L.or_launch.argtypes = [p, u64, i, u64, p, p, p]
             L.or_philox.restype = None
@@ -266,6 +268,12 @@ class OracleScene:
         seed = self.scene.seed if seed is None else seed
         lib().or_thermalize(self.h, int(seed), inst, int(pid), float(E0), int(n_coll), _ptr(out))
         return out
+
+    def trace(self, inst, pid, rows=64, seed=None):
+        out = np.zeros(rows * 10)
+        seed = self.scene.seed if seed is None else seed
+        lib().or_trace(self.h, int(seed), int(inst), int(pid), int(rows), _ptr(out))
+        return out.reshape(rows, 10)
 
     def launch(self, inst, pid, seed=None):
         p, d, E = np.zeros(3), np.zeros(3), np.zeros(1)

@@ -740,7 +740,21 @@ typedef struct {
 
 static double speed_of_E(double E, double m) { return sqrt(2.0 * E / (m * c_energy())); }
 
-static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid, outcome_t* o)
+/* optional trace: rows of (x,y,z, dx,dy,dz, speed, status, a, t); row 0 = launch
+ * (status -1), row r = state after flight r (status 0 collided: position at the
+ * collision, direction/speed after it, a = partner attempts, t = flight length;
+ * 1 landed: hit point, a = primitive, t = hit distance; 2 timed out) */
+static void trace_row(double* tr, int rows, int r, const double p[3], const double d[3], double speed, int status,
+                      double a, double t)
+{
+    if (!tr || r >= rows) return;
+    double* q = tr + 10 * r;
+    q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+    q[3] = d[0]; q[4] = d[1]; q[5] = d[2];
+    q[6] = speed; q[7] = status; q[8] = a; q[9] = t;
+}
+
+static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid, outcome_t* o, double* tr, int rows)
 {
     const inst_t* I = &S->inst[ii];
     const cath_t* c = &S->cath[I->cathode];
@@ -765,6 +779,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
     double speed = speed_of_E(E, c->mass);
     int64_t ncoll = 0, attempts = 0;
     double score = 0.0;
+    trace_row(tr, rows, 0, p, d, speed, -1, 0.0, 0.0);
 
     for (uint32_t k = 1;; ++k) {
         draw(&st, k, 0u, w);
@@ -776,6 +791,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         if (hit >= 0) {
             score -= t / lam;
             double q[3] = {p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2]};
+            trace_row(tr, rows, (int)k, q, d, speed, 1, hit, t);
             o->prim = hit;
             o->cell = -1;
             o->cosang = 0.0;
@@ -805,6 +821,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         for (int a = 0; a < 3; ++a) p[a] += ell * d[a];
         score += 1.0 - ell / lam;
         if ((int64_t)k > S->max_collisions) {
+            trace_row(tr, rows, (int)k, p, d, speed, 2, 0.0, ell);
             o->prim = -1;
             o->cell = -1;
             o->E = 0.5 * c->mass * speed * speed * c_energy();
@@ -816,11 +833,13 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         }
         for (int a = 0; a < 3; ++a) v[a] = speed * d[a];
         double V[3], vo[3], Vo[3];
-        attempts += sample_partner(S, c, &st, k, rn(w[3]), v, V);
+        int na = sample_partner(S, c, &st, k, rn(w[3]), v, V);
+        attempts += na;
         collide_with(S, c, v, V, rn(w[1]), rn(w[2]), vo, Vo, NULL);
         speed = sqrt(dot3(vo, vo));
         for (int a = 0; a < 3; ++a) d[a] = vo[a] / speed;
         ++ncoll;
+        trace_row(tr, rows, (int)k, p, d, speed, 0, na, ell);
     }
 }
 
@@ -966,7 +985,7 @@ static void* run_worker(void* arg)
     run_job* j = (run_job*)arg;
     for (int64_t i = j->begin; i < j->end; ++i) {
         outcome_t o;
-        transport_one(j->S, j->seed, j->inst[i], j->pid[i], &o);
+        transport_one(j->S, j->seed, j->inst[i], j->pid[i], &o, NULL, 0);
         j->prim[i] = o.prim;
         j->cell[i] = o.cell;
         j->E[i] = o.E;
@@ -1077,6 +1096,17 @@ void or_launch(const or_scene* S, uint64_t seed, int ii, uint64_t pid, double* p
         p[a] = c->c[a] + r * cos(al) * c->e1[a] + r * sin(al) * c->e2[a];
         d[a] = s * cos(ph) * c->e1[a] + s * sin(ph) * c->e2[a] + mu * c->n[a];
     }
+}
+
+/* per-flight trace of particle (inst, pid): rows x 10 doubles, unused rows status -2 */
+void or_trace(const or_scene* S, uint64_t seed, int inst, uint64_t pid, int rows, double* out)
+{
+    for (int r = 0; r < rows; ++r) {
+        memset(out + 10 * r, 0, 10 * sizeof(double));
+        out[10 * r + 7] = -2.0;
+    }
+    outcome_t o;
+    transport_one(S, seed, inst, pid, &o, out, rows);
 }
 
 /* quadrature self-test integrands */

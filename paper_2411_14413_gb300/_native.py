@@ -81,7 +81,8 @@ PRIM_KIND = {"box": 0, "rect": 1, "disc": 2, "cylinder": 3}
 INTERACTION = {"moliere": 0, "hard_sphere": 1}
 GAS_MOTION = {"thermal": 0, "stationary": 1}
 COUNT_TYPE = {"int32": 0, "int64": 1}
-PROBE = {"chi": 0, "bmax": 1, "K": 2, "M": 3, "launch": 4}
+PROBE = {"chi": 0, "bmax": 1, "K": 2, "M": 3, "launch": 4, "trace": 5}
+TRACE_ROWS = 64
 
 D3 = C.c_double * 3
 

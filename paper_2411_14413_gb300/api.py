@@ -129,11 +129,16 @@ def sput_scene_destroy(handle):
 def sput_probe(handle, what, idx, x):
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = len(x) // 2 if what == "chi" else len(x)
-    y = np.zeros(n * (7 if what == "launch" else 1), dtype=np.float64)
+    width = {"launch": 7, "trace": N.TRACE_ROWS * 10}.get(what, 1)
+    y = np.zeros(n * width, dtype=np.float64)
     rc = _lib().sput_probe(handle, N.PROBE[what], int(idx), int(n), x.ctypes.data_as(C.c_void_p),
                            y.ctypes.data_as(C.c_void_p))
     N.check(rc, "sput_probe")
-    return y.reshape(n, 7) if what == "launch" else y
+    if what == "launch":
+        return y.reshape(n, 7)
+    if what == "trace":
+        return y.reshape(n, N.TRACE_ROWS, 10)
+    return y
 
 
 def run_opts(seed=0, ticket_begin=0, ticket_end=0, accumulate=False, block_threads=0, blocks_per_sm=0,

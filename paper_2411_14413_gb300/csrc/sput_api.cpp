@@ -377,7 +377,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     // cathodes
     const int rt_n = 256;
     S->dcath.resize(S->cathodes.size());
-    S->rt.resize(S->cathodes.size() * (rt_n + 1));
+    S->rt.resize(S->cathodes.size() * 2 * (rt_n + 1));
     for (size_t c = 0; c < S->cathodes.size(); ++c) {
         const sput_cathode& C = S->cathodes[c];
         DevCathode& D = S->dcath[c];
@@ -390,13 +390,18 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
             D.e2[a] = (float)e2[a];
         }
         const double k = 1.0 / (C.rt_sigma * std::sqrt(2.0));
+        const double z0 = C.rt_r0 * k, zR = (C.rt_R - C.rt_r0) * k;
         D.rt_r0 = (float)C.rt_r0;
         D.rt_R = (float)C.rt_R;
         D.rt_k = (float)k;
         D.rt_A = (float)(C.rt_sigma * C.rt_sigma);
-        D.rt_C = (float)std::exp(-C.rt_r0 * C.rt_r0 * k * k);
         D.rt_B = (float)(C.rt_r0 * C.rt_sigma * std::sqrt(kPi / 2.0));
-        D.rt_E0 = (float)std::erf(C.rt_r0 * k);
+        D.rt_C0 = (float)std::exp(-z0 * z0);
+        D.rt_E0 = (float)std::erf(z0);
+        D.rt_Ec0 = (float)std::erfc(z0);
+        D.rt_CR = (float)std::exp(-zR * zR);
+        D.rt_EcR = (float)std::erfc(zR);
+        D.rt_pad = 0.0f;
         D.rt_FR = (float)racetrack_F64(C.rt_r0, C.rt_sigma, C.rt_R);
         double norm = 0.0;
         bool pure = true;
@@ -409,8 +414,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         D.cos_general = pure ? 0 : 1;
         D.target = C.target;
         D.pair = cath_pair[c];
-        D.rt_tab = (int)(c * (rt_n + 1));
-        racetrack_guess(C.rt_r0, C.rt_sigma, C.rt_R, rt_n, &S->rt[c * (rt_n + 1)]);
+        D.rt_tab = (int)(c * 2 * (rt_n + 1));
+        racetrack_guess(C.rt_r0, C.rt_sigma, C.rt_R, rt_n, &S->rt[c * 2 * (rt_n + 1)]);
         D.v_per_sqrtE = (float)std::sqrt(2.0 / (C.mass * kEnergyUnit));
         D.E_per_v2 = (float)(0.5 * C.mass * kEnergyUnit);
     }
@@ -782,16 +787,17 @@ void sput_scene_destroy(sput_scene* S)
 sput_status sput_probe(sput_scene* S, int what, int idx, int n, const double* x, double* y)
 {
     if (!S || !x || !y || n < 0) return fail(SPUT_ERR_INVALID_ARG, "NULL argument or negative n");
-    if (what < SPUT_PROBE_CHI || what > SPUT_PROBE_LAUNCH) return fail(SPUT_ERR_INVALID_ARG, "unknown probe");
+    if (what < SPUT_PROBE_CHI || what > SPUT_PROBE_TRACE) return fail(SPUT_ERR_INVALID_ARG, "unknown probe");
     if ((what == SPUT_PROBE_K || what == SPUT_PROBE_M) && (idx < 0 || idx >= (int)S->dpairs.size()))
         return fail(SPUT_ERR_INVALID_ARG, "pair index out of range");
-    if (what == SPUT_PROBE_LAUNCH && (idx < 0 || idx >= (int)S->dinst.size()))
+    if ((what == SPUT_PROBE_LAUNCH || what == SPUT_PROBE_TRACE) && (idx < 0 || idx >= (int)S->dinst.size()))
         return fail(SPUT_ERR_INVALID_ARG, "instance index out of range");
     if ((what == SPUT_PROBE_CHI || what == SPUT_PROBE_BMAX) && !S->bt)
         return fail(SPUT_ERR_UNSUPPORTED, "no Moliere tables in a hard-sphere scene");
     if (n == 0) return SPUT_OK;
     DeviceGuard guard(S->device);
-    const size_t nx = (size_t)n * (what == SPUT_PROBE_CHI ? 2 : 1), ny = (size_t)n * (what == SPUT_PROBE_LAUNCH ? 7 : 1);
+    const size_t nx = (size_t)n * (what == SPUT_PROBE_CHI ? 2 : 1);
+    const size_t ny = (size_t)n * (what == SPUT_PROBE_LAUNCH ? 7 : (what == SPUT_PROBE_TRACE ? kTraceRows * 10 : 1));
     double *dx = nullptr, *dy = nullptr;
     CUDA_TRY(cudaMalloc(&dx, nx * sizeof(double)));
     cudaError_t e = cudaMalloc(&dy, ny * sizeof(double));

@@ -49,16 +49,19 @@ struct alignas(16) DevGeom {
 
 struct alignas(16) DevCathode {
     float c[3], n[3], e1[3], e2[3];
-    // racetrack: radial pdf ~ r exp(-z^2), z = (r - r0) k, k = 1/(sigma sqrt 2), on [0, R];
-    // CDF numerator F(r) = A (C - exp(-z^2)) + B (erf(z) + E0), FR = F(R)
+    // racetrack: radial pdf ~ r exp(-z^2), z = (r - r0) k, k = 1/(sigma sqrt 2), on [0, R].
+    // Mass below r:  L(r) = A (C0 - e^{-z^2}) + B (erf z + erf z0)   [z0 = r0 k]
+    // Mass above r:  U(r) = A (e^{-z^2} - CR) + B (erfc z - erfc zR) [zR = (R - r0) k]
+    // with A = sigma^2, B = r0 sigma sqrt(pi/2); FR = L(R).
     float rt_r0, rt_R, rt_FR, rt_A;
-    float rt_B, rt_C, rt_E0, rt_k;
+    float rt_B, rt_C0, rt_k, rt_E0;        // rt_C0 = e^{-z0^2}, rt_E0 = erf z0
+    float rt_Ec0, rt_CR, rt_EcR, rt_pad;   // erfc z0, e^{-zR^2}, erfc zR
     float coef[6];
     float coef_norm;                       // sum c_i/(i+1)
     int cos_general;                       // 0 = pure cosine (mu = sqrt(u))
     int target;                            // local index of the target disc
     int pair;                              // interaction pair (tables)
-    int rt_tab;                            // offset of this cathode's racetrack guess table
+    int rt_tab;                            // offset of this cathode's two racetrack guess tables
     int pad0;
     float v_per_sqrtE;                     // speed (km/s) = v_per_sqrtE * sqrt(E / eV)
     float E_per_v2;                        // E (eV) = E_per_v2 * v^2
@@ -141,6 +144,8 @@ struct Params {
 };
 
 constexpr int kNumStats = 6;
+// rows of one SPUT_PROBE_TRACE record (launch state + 63 flights)
+constexpr int kTraceRows = 64;
 
 // Launchers implemented in sput_transport.cu.
 int transport_configure(int max_dynamic_smem);

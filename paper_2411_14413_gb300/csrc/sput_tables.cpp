@@ -340,18 +340,21 @@ double racetrack_F64(double r0, double sg, double r)
 
 void racetrack_guess(double r0, double sg, double R, int n, float* out)
 {
+    // out[0..n]: r at u = (j/n)^2; out[n+1..2n+1]: r at u = 1 - (j/n)^2
     double FR = racetrack_F64(r0, sg, R);
-    for (int j = 0; j <= n; ++j) {
-        double u = (double)j / n;
-        u *= u;
-        double tgt = u * FR, lo = 0.0, hi = R;
-        for (int it = 0; it < 100; ++it) {
-            double m = 0.5 * (lo + hi);
-            if (racetrack_F64(r0, sg, m) < tgt) lo = m;
-            else hi = m;
+    for (int half = 0; half < 2; ++half)
+        for (int j = 0; j <= n; ++j) {
+            double q = (double)j / n;
+            q *= q;
+            double u = half ? 1.0 - q : q;
+            double tgt = u * FR, lo = 0.0, hi = R;
+            for (int it = 0; it < 100; ++it) {
+                double m = 0.5 * (lo + hi);
+                if (racetrack_F64(r0, sg, m) < tgt) lo = m;
+                else hi = m;
+            }
+            out[half * (n + 1) + j] = (float)(0.5 * (lo + hi));
         }
-        out[j] = (float)(0.5 * (lo + hi));
-    }
 }
 
 }  // namespace sput

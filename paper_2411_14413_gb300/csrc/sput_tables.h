@@ -67,7 +67,7 @@ double K64(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_therma
 double M64(const PairPhys& pp, const BmaxTable* bt, double s_gas, double v, int monotone);
 int h_monotone(const PairPhys& pp, const BmaxTable* bt, double g_top);
 
-// Racetrack inverse-CDF guesses at u = (j/n)^2, j = 0..n.
+// Racetrack inverse-CDF guesses: n+1 values at u = (j/n)^2, then n+1 at u = 1 - (j/n)^2.
 void racetrack_guess(double r0, double sigma, double R, int n, float* out);
 double racetrack_F64(double r0, double sigma, double r);
 

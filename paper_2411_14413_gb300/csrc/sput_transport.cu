@@ -174,20 +174,34 @@ struct Lane {
 
 __device__ float racetrack_r(const DevCathode& C, const float* rt_tab, int rt_n, float u)
 {
-    // table guess in sqrt(u), then Newton on the closed-form CDF numerator
-    float x = sqrtf(u) * (float)rt_n;
+    // Invert the radial CDF: guess from a table in sqrt(u) (lower half) or
+    // sqrt(1-u) (upper half), then Newton on the log of the lower or upper
+    // mass, both written without cancellation (erfc in the tails).
+    const bool upper = u > 0.5f;
+    const float q = upper ? 1.0f - u : u;  // exact for RN = m 2^-24
+    if (q <= 0.0f) return C.rt_R;
+    float x = sqrtf(q) * (float)rt_n;
     int j = min((int)x, rt_n - 1);
     float f = x - (float)j;
-    const float* g = rt_tab + C.rt_tab;
+    const float* g = rt_tab + C.rt_tab + (upper ? rt_n + 1 : 0);
     float r = fmaf(f, g[j + 1] - g[j], g[j]);
-    const float T = u * C.rt_FR;
-#pragma unroll
-    for (int it = 0; it < 3; ++it) {
-        float z = (r - C.rt_r0) * C.rt_k;
-        float e = expf(-z * z);
-        float F = fmaf(C.rt_A, C.rt_C - e, C.rt_B * (erff(z) + C.rt_E0));
-        float pdf = r * e;
-        if (pdf > 1e-30f) r -= (F - T) / pdf;
+    const float lt = logf(q * C.rt_FR);
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+        const float z = (r - C.rt_r0) * C.rt_k;
+        const float e = expf(-z * z);
+        const float pdf = r * e;
+        float mass, dlog;
+        if (!upper) {
+            const float t2 = z <= 0.0f ? erfcf(-z) - C.rt_Ec0 : erff(z) + C.rt_E0;
+            mass = fmaf(C.rt_A, C.rt_C0 - e, C.rt_B * t2);
+            dlog = pdf / mass;
+        } else {
+            mass = fmaf(C.rt_A, e - C.rt_CR, C.rt_B * (erfcf(z) - C.rt_EcR));
+            dlog = -pdf / mass;
+        }
+        if (!(mass > 0.0f) || !(pdf > 0.0f)) break;
+        r -= (logf(mass) - lt) / dlog;
         r = fminf(fmaxf(r, 0.0f), C.rt_R);
     }
     return r;
@@ -287,6 +301,159 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
         }
     }
     return t;
+}
+
+// ------------------------------------------------------------- particle start
+__device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, uint32_t inst, uint32_t pid,
+                               unsigned long long ticket)
+{
+    const DevInstance& I = P.inst[inst];
+    const DevGeom G = geoms[I.geometry];
+    const DevCathode& C = P.cath[I.cathode];
+    S.inst = inst;
+    S.pid = pid;
+    S.ticket = ticket;
+    S.gbegin = G.begin;
+    S.gcount = G.count;
+    S.gsub = G.substrate;
+    S.target = C.target;
+    S.pair = I.pair;
+    S.ng14 = I.ng14;
+    S.E_per_v2 = C.E_per_v2;
+    float E;
+    launch_state(P, P.rt_tab, inst, pid, S.px, S.py, S.pz, S.dx, S.dy, S.dz, E);
+    S.speed = C.v_per_sqrtE * sqrtf(E);
+    S.k = 0u;
+    S.ncoll = 0u;
+    S.score = 0.0f;
+}
+
+// ------------------------------------------------------------- one flight
+enum { kStepCollided = 0, kStepLanded = 1, kStepTimedOut = 2 };
+
+struct StepOut {
+    float t;        // landing: distance to the hit; otherwise the flight length
+    int prim;       // landing: local primitive index
+    int attempts;   // partner attempts of this collision
+    int nonfinite;  // the state became NaN/Inf
+};
+
+// Flight k+1 of the atom in S: free path, surface test, then either the
+// landing (S keeps the pre-flight position; out.t is the hit distance) or the
+// move to the collision point and the binary collision with a gas atom.
+__device__ int flight_step(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
+                           StepOut& out)
+{
+    S.k += 1u;
+    out.attempts = 0;
+    out.nonfinite = 0;
+    out.prim = -1;
+    const uint4 w = philox(P.key0, P.key1, S.pid, S.inst, S.k, 0u);
+    const DevPair pr = pairs[S.pair];
+    // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
+    const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
+    const float inv_lam = P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv;
+    const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
+
+    // surface test: nearest hit, ties to the lowest index; the emitting target
+    // is skipped on the first flight
+    float tb = CUDART_INF_F;
+    int hb = -1;
+    const int excl = S.k == 1u ? S.target : -1;
+    for (int li = 0; li < S.gcount; ++li) {
+        if (li == excl) continue;
+        const float t = hit_prim(prims[S.gbegin + li], P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
+        if (t < tb) {
+            tb = t;
+            hb = li;
+        }
+    }
+    if (hb >= 0 && tb <= ell) {
+        S.score -= tb * inv_lam;
+        out.t = tb;
+        out.prim = hb;
+        return kStepLanded;
+    }
+
+    // move, then collide
+    out.t = ell;
+    S.px = fmaf(ell, S.dx, S.px);
+    S.py = fmaf(ell, S.dy, S.py);
+    S.pz = fmaf(ell, S.dz, S.pz);
+    S.score += 1.0f - ell * inv_lam;
+    if (!isfinite(S.px + S.py + S.pz + S.speed)) {
+        out.nonfinite = 1;
+        return kStepTimedOut;
+    }
+    if ((long long)S.k > P.max_collisions) return kStepTimedOut;
+
+    const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
+    float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
+    if (P.gas_thermal) {
+        // gas partner: Maxwellian weighted by sigma(g) g, rejection against M(v)
+        const float M = wtab_eval(T, pr, pr.M_off, S.speed);
+        uint4 wa = make_uint4(0u, 0u, 0u, 0u);
+        for (int a = 0; a < P.max_attempts; ++a) {
+            const uint4 wn = philox(P.key0, P.key1, S.pid, S.inst, S.k, 1u + (uint32_t)a);
+            const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
+            const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
+            float s1, c1;
+            sincospif(2.0f * rn(wn.y), &s1, &c1);
+            const float c3 = cospif(2.0f * rn(wn.w));
+            Vx = P.s_gas * R0 * c1;
+            Vy = P.s_gas * R0 * s1;
+            Vz = P.s_gas * R1 * c3;
+            float ua;
+            if (a == 0) ua = rn(w.w);
+            else {
+                const int q = (a - 1) & 3;
+                if (q == 0)
+                    wa = philox(P.key0, P.key1, S.pid, S.inst, S.k,
+                                1u + (uint32_t)P.max_attempts + (uint32_t)((a - 1) >> 2));
+                ua = rn(q == 0 ? wa.x : (q == 1 ? wa.y : (q == 2 ? wa.z : wa.w)));
+            }
+            const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
+            const float g2 = gx * gx + gy * gy + gz * gz;
+            ++out.attempts;
+            if (ua * M <= h_of_g(T, pr, sqrtf(g2), g2)) break;
+        }
+    }
+    // binary collision in the CM frame: rotate g = v - V by (chi, psi), |g| kept
+    const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    if (g2 > 0.0f) {
+        const float g = sqrtf(g2);
+        const float ig = 1.0f / g;
+        const float hx = gx * ig, hy = gy * ig, hz = gz * ig;
+        float chi;
+        if (pr.hard_sphere) {
+            chi = 2.0f * acosf(sqrtf(rn(w.y)));
+        } else {
+            const float eps = pr.kappa * g2;
+            const float le = logf(eps);
+            const float beta = bmax_eval(T, le) * sqrtf(rn(w.y));
+            chi = chi_moliere(eps, beta, xh_eval(T, le), P.gm);
+        }
+        float sc, cc, sp, cp;
+        sincosf(chi, &sc, &cc);
+        sincospif(2.0f * rn(w.z), &sp, &cp);
+        float3 b1, b2;
+        onb(hx, hy, hz, b1, b2);
+        const float gpx = g * (cc * hx + sc * (cp * b1.x + sp * b2.x));
+        const float gpy = g * (cc * hy + sc * (cp * b1.y + sp * b2.y));
+        const float gpz = g * (cc * hz + sc * (cp * b1.z + sp * b2.z));
+        const float nvx = pr.m1M * vx + pr.m2M * Vx + pr.m2M * gpx;
+        const float nvy = pr.m1M * vy + pr.m2M * Vy + pr.m2M * gpy;
+        const float nvz = pr.m1M * vz + pr.m2M * Vz + pr.m2M * gpz;
+        const float sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
+        S.speed = sqrtf(sp2);
+        const float is = 1.0f / S.speed;
+        S.dx = nvx * is;
+        S.dy = nvy * is;
+        S.dz = nvz * is;
+    }
+    ++S.ncoll;
+    return kStepCollided;
 }
 
 // ------------------------------------------------------------- kernel
@@ -412,57 +579,22 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params P)
                     if (s_prefix[mid] <= t) lo = mid;
                     else hi = mid;
                 }
-                const DevInstance& I = P.inst[lo];
-                const DevGeom G = s_geoms[I.geometry];
-                const DevCathode& C = P.cath[I.cathode];
-                S.inst = (uint32_t)lo;
-                S.pid = (uint32_t)(t - s_prefix[lo]);
-                S.ticket = t;
-                S.gbegin = G.begin;
-                S.gcount = G.count;
-                S.gsub = G.substrate;
-                S.target = C.target;
-                S.pair = I.pair;
-                S.ng14 = I.ng14;
-                S.E_per_v2 = C.E_per_v2;
-                float E;
-                launch_state(P, P.rt_tab, S.inst, S.pid, S.px, S.py, S.pz, S.dx, S.dy, S.dz, E);
-                S.speed = C.v_per_sqrtE * sqrtf(E);
-                S.k = 0u;
-                S.ncoll = 0u;
-                S.score = 0.0f;
+                start_particle(S, P, s_geoms, (uint32_t)lo, (uint32_t)(t - s_prefix[lo]), t);
                 alive = true;
             }
         }
         if (!__any_sync(kFull, alive)) break;
         if (!alive) continue;
 
-        // ---------------------------------------------------- free flight
-        S.k += 1u;
+        // ---------------------------------------------------- one flight
         ++c_flights;
-        const uint4 w = philox(P.key0, P.key1, S.pid, S.inst, S.k, 0u);
-        const DevPair pr = s_pairs[S.pair];
-        // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
-        const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
-        const float inv_lam = P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv;
-        const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
-
-        // ---------------------------------------------------- surface test
-        float tb = CUDART_INF_F;
-        int hb = -1;
-        const int excl = S.k == 1u ? S.target : -1;
-        for (int li = 0; li < S.gcount; ++li) {
-            if (li == excl) continue;
-            const float t = hit_prim(s_prims[S.gbegin + li], P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
-            if (t < tb) {
-                tb = t;
-                hb = li;
-            }
-        }
-
-        if (hb >= 0 && tb <= ell) {
-            // ------------------------------------------------ landing
-            S.score -= tb * inv_lam;
+        StepOut so;
+        const int res = flight_step(S, P, T, s_prims, s_pairs, so);
+        c_att += so.attempts;
+        if (res == kStepLanded) {
+            // ------------------------------------------------ landing tally
+            const float tb = so.t;
+            const int hb = so.prim;
             const float E = S.E_per_v2 * S.speed * S.speed;
             int cell = -1;
             float cosang = 0.0f;
@@ -517,16 +649,8 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params P)
             ++c_landed;
             ++c_particles;
             alive = false;
-            continue;
-        }
-
-        // ---------------------------------------------------- move, then collide
-        S.px = fmaf(ell, S.dx, S.px);
-        S.py = fmaf(ell, S.dy, S.py);
-        S.pz = fmaf(ell, S.dz, S.pz);
-        S.score += 1.0f - ell * inv_lam;
-        if ((long long)S.k > P.max_collisions || !isfinite(S.px + S.py + S.pz + S.speed)) {
-            if (!isfinite(S.px + S.py + S.pz + S.speed)) atomicOr(P.status, kStatusNonFinite);
+        } else if (res == kStepTimedOut) {
+            if (so.nonfinite) atomicOr(P.status, kStatusNonFinite);
             if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + P.max_prims], 1u);
             else if (P.timed_out) atomicAdd(reinterpret_cast<unsigned long long*>(P.timed_out) + S.inst, 1ull);
             if (P.records) {
@@ -542,74 +666,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params P)
             ++c_timed;
             ++c_particles;
             alive = false;
-            continue;
+        } else {
+            ++c_coll;
         }
-
-        const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
-        float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
-        if (P.gas_thermal) {
-            // gas partner: Maxwellian weighted by sigma(g) g, rejection against M(v)
-            const float M = wtab_eval(T, pr, pr.M_off, S.speed);
-            uint4 wa = make_uint4(0u, 0u, 0u, 0u);
-            for (int a = 0; a < P.max_attempts; ++a) {
-                const uint4 wn = philox(P.key0, P.key1, S.pid, S.inst, S.k, 1u + (uint32_t)a);
-                const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
-                const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
-                float s1, c1;
-                sincospif(2.0f * rn(wn.y), &s1, &c1);
-                const float c3 = cospif(2.0f * rn(wn.w));
-                Vx = P.s_gas * R0 * c1;
-                Vy = P.s_gas * R0 * s1;
-                Vz = P.s_gas * R1 * c3;
-                float ua;
-                if (a == 0) ua = rn(w.w);
-                else {
-                    const int q = (a - 1) & 3;
-                    if (q == 0) wa = philox(P.key0, P.key1, S.pid, S.inst, S.k, 1u + (uint32_t)P.max_attempts + (uint32_t)((a - 1) >> 2));
-                    ua = rn(q == 0 ? wa.x : (q == 1 ? wa.y : (q == 2 ? wa.z : wa.w)));
-                }
-                const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
-                const float g2 = gx * gx + gy * gy + gz * gz;
-                ++c_att;
-                if (ua * M <= h_of_g(T, pr, sqrtf(g2), g2)) break;
-            }
-        }
-        // binary collision in the CM frame: rotate g = v - V by (chi, psi), |g| kept
-        const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
-        const float g2 = gx * gx + gy * gy + gz * gz;
-        if (g2 > 0.0f) {
-            const float g = sqrtf(g2);
-            const float ig = 1.0f / g;
-            const float hx = gx * ig, hy = gy * ig, hz = gz * ig;
-            float chi;
-            if (pr.hard_sphere) {
-                chi = 2.0f * acosf(sqrtf(rn(w.y)));
-            } else {
-                const float eps = pr.kappa * g2;
-                const float le = logf(eps);
-                const float beta = bmax_eval(T, le) * sqrtf(rn(w.y));
-                chi = chi_moliere(eps, beta, xh_eval(T, le), P.gm);
-            }
-            float sc, cc, sp, cp;
-            sincosf(chi, &sc, &cc);
-            sincospif(2.0f * rn(w.z), &sp, &cp);
-            float3 b1, b2;
-            onb(hx, hy, hz, b1, b2);
-            const float gpx = g * (cc * hx + sc * (cp * b1.x + sp * b2.x));
-            const float gpy = g * (cc * hy + sc * (cp * b1.y + sp * b2.y));
-            const float gpz = g * (cc * hz + sc * (cp * b1.z + sp * b2.z));
-            const float nvx = pr.m1M * vx + pr.m2M * Vx + pr.m2M * gpx;
-            const float nvy = pr.m1M * vy + pr.m2M * Vy + pr.m2M * gpy;
-            const float nvz = pr.m1M * vz + pr.m2M * Vz + pr.m2M * gpz;
-            const float sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
-            S.speed = sqrtf(sp2);
-            const float is = 1.0f / S.speed;
-            S.dx = nvx * is;
-            S.dy = nvy * is;
-            S.dz = nvz * is;
-        }
-        ++S.ncoll;
-        ++c_coll;
     }
 
     // ---------------------------------------------------- flush counters
@@ -662,6 +721,31 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         float val = wtab_eval(T, pr, what == SPUT_PROBE_K ? pr.K_off : pr.M_off, v);
         if (what == SPUT_PROBE_K && !P.gas_thermal) val *= v;  // the table holds sigma(v) = K/v
         y[i] = val;
+    } else if (what == SPUT_PROBE_TRACE) {
+        // state after each flight of particle x[i] of instance idx, kTraceRows rows of 10
+        Lane S;
+        start_particle(S, P, P.geoms, (uint32_t)idx, (uint32_t)x[i], 0ull);
+        double* o = y + (size_t)i * kTraceRows * 10;
+        for (int r = 0; r < kTraceRows * 10; ++r) o[r] = 0.0;
+        o[0] = S.px; o[1] = S.py; o[2] = S.pz; o[3] = S.dx; o[4] = S.dy; o[5] = S.dz; o[6] = S.speed; o[7] = -1.0;
+        int status = kStepCollided;
+        for (int r = 1; r < kTraceRows; ++r) {
+            double* q = o + (size_t)r * 10;
+            if (status != kStepCollided) {
+                q[7] = -2.0;
+                continue;
+            }
+            StepOut so;
+            status = flight_step(S, P, T, P.prims, P.pairs, so);
+            float px = S.px, py = S.py, pz = S.pz;
+            if (status == kStepLanded) {
+                px = fmaf(so.t, S.dx, S.px);
+                py = fmaf(so.t, S.dy, S.py);
+                pz = fmaf(so.t, S.dz, S.pz);
+            }
+            q[0] = px; q[1] = py; q[2] = pz; q[3] = S.dx; q[4] = S.dy; q[5] = S.dz; q[6] = S.speed;
+            q[7] = status; q[8] = status == kStepLanded ? so.prim : so.attempts; q[9] = so.t;
+        }
     } else if (what == SPUT_PROBE_LAUNCH) {
         float px, py, pz, dx, dy, dz, E;
         launch_state(P, P.rt_tab, (uint32_t)idx, (uint32_t)x[i], px, py, pz, dx, dy, dz, E);
