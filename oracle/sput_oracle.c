@@ -147,21 +147,27 @@ static double gl_panel(fn1 f, const void* ctx, double a, double b)
     return s * h;
 }
 
-static double adapt_rec(fn1 f, const void* ctx, double a, double b, double whole, double tol, int depth)
+static double adapt_rec(fn1 f, const void* ctx, double a, double b, double whole, double tol, int depth, int* budget)
 {
     double m = 0.5 * (a + b);
     double l = gl_panel(f, ctx, a, m), r = gl_panel(f, ctx, m, b);
-    if (depth <= 0 || fabs(l + r - whole) <= tol) return l + r;
-    return adapt_rec(f, ctx, a, m, l, 0.5 * tol, depth - 1) + adapt_rec(f, ctx, m, b, r, 0.5 * tol, depth - 1);
+    *budget -= 2;
+    /* stop refining on a non-finite value or when the panel budget is spent */
+    if (!isfinite(l + r) || depth <= 0 || *budget <= 0 || fabs(l + r - whole) <= tol) return l + r;
+    return adapt_rec(f, ctx, a, m, l, 0.5 * tol, depth - 1, budget) +
+           adapt_rec(f, ctx, m, b, r, 0.5 * tol, depth - 1, budget);
 }
 
-/* integral of f over [a,b]; panels are halved until two levels agree to tol */
+/* integral of f over [a,b]; panels are halved until two levels agree to tol
+ * (at most 20000 panels per call) */
 static double integrate(fn1 f, const void* ctx, double a, double b, double rel_tol)
 {
     pthread_once(&gl_once, gl_init);
     double whole = gl_panel(f, ctx, a, b);
+    if (!isfinite(whole)) return whole;
     double tol = rel_tol * fabs(whole) + 1e-300;
-    return adapt_rec(f, ctx, a, b, whole, tol, 40);
+    int budget = 20000;
+    return adapt_rec(f, ctx, a, b, whole, tol, 40, &budget);
 }
 
 double or_integrate_test(int which, double a, double b);
@@ -445,7 +451,8 @@ static double sigma_of_g(const or_scene* S, const cath_t* c, double g)
     if (S->interaction == INT_HARD_SPHERE) return M_PI * S->hs_diameter * S->hs_diameter;
     double Er = 0.5 * c->mu_red * g * g * c_energy();
     double eps = c->a_scr * Er / c->zze2;
-    if (!(eps > 0.0)) eps = 1e-300;
+    /* floor far below any reachable collision (g < 1e-9 km/s) keeps the root finding finite */
+    if (!(eps > 1e-40)) eps = 1e-40;
     double bm = or_bmax_interp(S->chi_min, eps) * c->a_scr;
     return M_PI * bm * bm;
 }
