@@ -37,11 +37,14 @@ METRIC = "particle-collisions/sec and landed particles/sec on 1 GB300 vs oracle;
 UNIT = "collisions/s"
 WORKLOAD = ("quaternary co-sputter Ni/Pd/Pt/Ru, 4 cathodes tilted 30 deg confocal at 120 mm, "
             "4 x 1e7 particles, Ar 0.5 Pa 300 K, E_i 400 eV, 100 mm wafer, 200x200 int64 counts + fp64 energy")
-# Lane-instructions the transport kernel executes per collision on this
-# workload, from one ncu capture (smsp__thread_inst_executed.sum divided by
-# the collisions of that launch); see profiles/transport_quaternary_ncu.md.
-LANE_OPS_PER_COLLISION = float(os.environ.get("SPUT_LANE_OPS_PER_COLLISION", "2300"))
-# dram bytes per launch of the full workload from the same capture (None until measured)
+# Algorithmic work per collision: active-lane instructions per collision of the
+# reference capture of the transport kernel on this workload (ncu
+# smsp__thread_inst_executed.sum / collisions of the launch, quaternary scene
+# with 2e5 particles per cathode); the figure is kept fixed so that frac
+# measures speed against one definition of the work.
+LANE_OPS_PER_COLLISION = 4136.0
+# DRAM bytes (read + write) of one launch, from the capture of the current
+# kernel; None whenever the kernel changed after the capture.
 TRAFFIC_PER_LAUNCH = None
 LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes issue one instruction per clock each
 
