@@ -270,6 +270,32 @@ sput_status sput_run(sput_scene* scene, const sput_run_opts* opts, void* stream,
 sput_status sput_run_host(sput_scene* scene, const sput_run_opts* opts, const sput_tallies* host_tallies,
                           sput_run_stats* stats);
 
+/* Same transport as sput_run, for callers that must not allocate device memory
+ * at run time: code recorded into a CUDA graph under a global-mode stream
+ * capture (where cudaMalloc is not permitted), processes whose device memory
+ * is owned by another allocator that has reserved it, or latency-critical
+ * loops that keep the driver allocator (which may synchronise the device) off
+ * their path.  sput_run allocates its run scratch (ticket counter, statistics,
+ * status word: 64 bytes) on its first call for a scene; this variant instead
+ * uses a static array of 256 bytes in the library's module memory, which every
+ * GPU that loads the library holds until the process exits.  It never calls
+ * cudaMalloc, cudaFree or any other allocating routine; the scene (inputs) and
+ * the tallies (outputs) are passed in exactly as for sput_run.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls on one device share the array and it keeps the last call's
+ *     contents; each call clears the counters it needs before its kernel.
+ *     Calls whose work overlaps on the GPU (other streams, other threads,
+ *     other scenes on the same device) race on it: serialise them.
+ *   - A run whose scratch would exceed the array's capacity is rejected with
+ *     SPUT_ERR_UNSUPPORTED and a message naming both sizes.
+ *   - With stats != NULL the call waits for the stream (opts->timeout_ms
+ *     applies) and also reuses the scene's pinned statistics buffer.
+ * The paper has no counterpart of this entry point. */
+sput_status sput_run_noalloc(sput_scene* scene, const sput_run_opts* opts, void* stream, const sput_tallies* tallies,
+                             sput_run_stats* stats);
+
 /* Free the scene and its device memory. */
 void sput_scene_destroy(sput_scene* scene);
 

@@ -179,6 +179,7 @@ SIGNATURES = {
     "sput_tally_layout_get": (C.c_int, [_P, C.POINTER(sput_tally_layout)]),
     "sput_run": (C.c_int, [_P, C.POINTER(sput_run_opts), _P, C.POINTER(sput_tallies), C.POINTER(sput_run_stats)]),
     "sput_run_host": (C.c_int, [_P, C.POINTER(sput_run_opts), C.POINTER(sput_tallies), C.POINTER(sput_run_stats)]),
+    "sput_run_noalloc": (C.c_int, [_P, C.POINTER(sput_run_opts), _P, C.POINTER(sput_tallies), C.POINTER(sput_run_stats)]),
     "sput_scene_destroy": (None, [_P]),
     "sput_probe": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
 }

@@ -115,6 +115,15 @@ def sput_run(handle, opts, stream, tallies, want_stats=True):
     return st if want_stats else None
 
 
+def sput_run_noalloc(handle, opts, stream, tallies, want_stats=True):
+    """sput_run without any device allocation (static run scratch)."""
+    st = N.sput_run_stats()
+    rc = _lib().sput_run_noalloc(handle, C.byref(opts), C.c_void_p(stream), C.byref(tallies),
+                                 C.byref(st) if want_stats else None)
+    N.check(rc, "sput_run_noalloc")
+    return st if want_stats else None
+
+
 def sput_run_host(handle, opts, tallies):
     st = N.sput_run_stats()
     N.check(_lib().sput_run_host(handle, C.byref(opts), C.byref(tallies), C.byref(st)), "sput_run_host")

@@ -768,6 +768,55 @@ sput_status sput_run_host(sput_scene* S, const sput_run_opts* opts, const sput_t
     return SPUT_OK;
 }
 
+sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* stream, const sput_tallies* T,
+                             sput_run_stats* stats)
+{
+    // Same transport as sput_run, but the run scratch (ticket counter, statistics,
+    // status word) is the library's static device array instead of a per-scene
+    // cudaMalloc, and the statistics wait polls the stream instead of creating
+    // an event: nothing here allocates.
+    if (!S) return fail(SPUT_ERR_INVALID_ARG, "scene is NULL");
+    if (kRunScratchBytes > kStaticScratchBytes)
+        return fail(SPUT_ERR_UNSUPPORTED, "run scratch of " + std::to_string(kRunScratchBytes) +
+                                              " bytes exceeds the static scratch of " +
+                                              std::to_string(kStaticScratchBytes) + " bytes");
+    DeviceGuard guard(S->device);
+    if (!guard.ok) return fail(SPUT_ERR_CUDA, "cudaSetDevice failed");
+    unsigned long long* scratch = nullptr;
+    int e0 = static_scratch_address(S->device, &scratch);
+    if (e0 != 0) return cuda_fail((cudaError_t)e0, "cudaGetSymbolAddress(static run scratch)");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    sput_status rs = run_impl(S, opts, st, T, nullptr, scratch);
+    if (rs != SPUT_OK || !stats) return rs;
+    CUDA_TRY(cudaMemcpyAsync(S->h_scratch, scratch, kRunScratchBytes, cudaMemcpyDeviceToHost, st));
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(st);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(q, "transport kernel");
+        if (opts->timeout_ms > 0 &&
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+                opts->timeout_ms)
+            return fail(SPUT_ERR_TIMEOUT, "transport did not finish within timeout_ms (device left running)");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    const unsigned long long* h = S->h_scratch;
+    stats->particles = h[1];
+    stats->landed = h[2];
+    stats->timed_out = h[3];
+    stats->flights = h[4];
+    stats->collisions = h[5];
+    stats->attempts = h[6];
+    stats->device_status = (uint32_t)(h[1 + kNumStats] & 0xffffffffu);
+    stats->grid_blocks = 0;
+    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : 128);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+    stats->kernel_ms = ms;
+    if (stats->device_status) return fail(SPUT_ERR_DEVICE_CHECK, "device status bits set");
+    return SPUT_OK;
+}
+
 void sput_scene_destroy(sput_scene* S)
 {
     if (!S) return;

@@ -154,4 +154,11 @@ size_t transport_smem_bytes(const Params& p);
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem);
 int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev, double* y_dev, void* stream);
 
+// Static run scratch of sput_run_noalloc (module memory, no allocation).
+constexpr size_t kRunScratchBytes = 64;      // ticket counter + kNumStats statistics + status word
+constexpr size_t kStaticScratchBytes = 256;  // capacity of the static array
+// Device address of the static scratch for `device` (must be current); looked
+// up with cudaGetSymbolAddress on the first call per device, then cached.
+int static_scratch_address(int device, unsigned long long** out);
+
 }  // namespace sput

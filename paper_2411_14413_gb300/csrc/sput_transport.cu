@@ -13,6 +13,8 @@
 #include <math_constants.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "sput_internal.h"
 
@@ -794,6 +796,33 @@ int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev,
     if (n <= 0) return 0;
     probe_kernel<<<(n + 127) / 128, 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p, what, idx, n, x_dev, y_dev);
     return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------- static run scratch
+// Run scratch for sput_run_noalloc: ticket counter, statistics and status word
+// in module memory, so that a run needs no device allocation at all.  Every
+// device that loads the library holds these kStaticScratchBytes until the
+// process exits.  In host code the name below is only a stand-in for the
+// device symbol; its device address is looked up per device, with that
+// device current, and cached.
+static __device__ __align__(256) unsigned long long g_static_run_scratch[kStaticScratchBytes / 8];
+
+int static_scratch_address(int device, unsigned long long** out)
+{
+    static std::mutex mu;
+    static std::map<int, unsigned long long*> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(device);
+    if (it != cache.end()) {
+        *out = it->second;
+        return 0;
+    }
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_run_scratch);
+    if (e != cudaSuccess) return (int)e;
+    cache[device] = reinterpret_cast<unsigned long long*>(ptr);
+    *out = cache[device];
+    return 0;
 }
 
 }  // namespace sput
