@@ -93,7 +93,7 @@ struct sput_scene {
     std::vector<DevInstance> dinst;
     std::vector<unsigned long long> prefix;
     std::vector<float4> wtab;
-    std::vector<float> rt;
+    std::vector<float4> rt;
     std::vector<PairPhys> pair_phys;
     std::vector<int> pair_monotone;
     std::vector<double> pair_E_top;
@@ -375,9 +375,9 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     }
 
     // cathodes
-    const int rt_n = 256;
+    const int rt_n = 512;
     S->dcath.resize(S->cathodes.size());
-    S->rt.resize(S->cathodes.size() * 2 * (rt_n + 1));
+    S->rt.clear();
     for (size_t c = 0; c < S->cathodes.size(); ++c) {
         const sput_cathode& C = S->cathodes[c];
         DevCathode& D = S->dcath[c];
@@ -389,20 +389,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
             D.e1[a] = (float)C.e1[a];
             D.e2[a] = (float)e2[a];
         }
-        const double k = 1.0 / (C.rt_sigma * std::sqrt(2.0));
-        const double z0 = C.rt_r0 * k, zR = (C.rt_R - C.rt_r0) * k;
-        D.rt_r0 = (float)C.rt_r0;
         D.rt_R = (float)C.rt_R;
-        D.rt_k = (float)k;
-        D.rt_A = (float)(C.rt_sigma * C.rt_sigma);
-        D.rt_B = (float)(C.rt_r0 * C.rt_sigma * std::sqrt(kPi / 2.0));
-        D.rt_C0 = (float)std::exp(-z0 * z0);
-        D.rt_E0 = (float)std::erf(z0);
-        D.rt_Ec0 = (float)std::erfc(z0);
-        D.rt_CR = (float)std::exp(-zR * zR);
-        D.rt_EcR = (float)std::erfc(zR);
-        D.rt_pad = 0.0f;
-        D.rt_FR = (float)racetrack_F64(C.rt_r0, C.rt_sigma, C.rt_R);
+        for (int q = 0; q < 11; ++q) D.rt_pad[q] = 0.0f;
         double norm = 0.0;
         bool pure = true;
         for (int i = 0; i < 6; ++i) {
@@ -414,8 +402,21 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         D.cos_general = pure ? 0 : 1;
         D.target = C.target;
         D.pair = cath_pair[c];
-        D.rt_tab = (int)(c * 2 * (rt_n + 1));
-        racetrack_guess(C.rt_r0, C.rt_sigma, C.rt_R, rt_n, &S->rt[c * 2 * (rt_n + 1)]);
+        // cathodes with the same racetrack profile share one table
+        int same = -1;
+        for (size_t c2 = 0; c2 < c; ++c2)
+            if (S->cathodes[c2].rt_r0 == C.rt_r0 && S->cathodes[c2].rt_sigma == C.rt_sigma &&
+                S->cathodes[c2].rt_R == C.rt_R) {
+                same = (int)c2;
+                break;
+            }
+        if (same >= 0) {
+            D.rt_tab = S->dcath[same].rt_tab;
+        } else {
+            D.rt_tab = (int)S->rt.size();
+            S->rt.resize(S->rt.size() + 2 * rt_n);
+            racetrack_table(C.rt_r0, C.rt_sigma, C.rt_R, rt_n, &S->rt[D.rt_tab]);
+        }
         D.v_per_sqrtE = (float)std::sqrt(2.0 / (C.mass * kEnergyUnit));
         D.E_per_v2 = (float)(0.5 * C.mass * kEnergyUnit);
     }
@@ -446,7 +447,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->off_bm = place(sizeof(float4) * bm.size());
     S->off_xh = place(sizeof(float) * xh.size());
     S->off_w = place(sizeof(float4) * S->wtab.size());
-    S->off_rt = place(sizeof(float) * S->rt.size());
+    S->off_rt = place(sizeof(float4) * S->rt.size());
     S->blob_bytes = o;
     cudaError_t e = cudaMalloc(&S->d_blob, S->blob_bytes);
     if (e != cudaSuccess) {
@@ -466,7 +467,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     put(S->off_bm, bm.data(), sizeof(float4) * bm.size());
     put(S->off_xh, xh.data(), sizeof(float) * xh.size());
     put(S->off_w, S->wtab.data(), sizeof(float4) * S->wtab.size());
-    put(S->off_rt, S->rt.data(), sizeof(float) * S->rt.size());
+    put(S->off_rt, S->rt.data(), sizeof(float4) * S->rt.size());
     e = cudaMemcpy(S->d_blob, h.data(), S->blob_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_scratch, 64);
     if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
@@ -487,7 +488,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.bm_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_bm);
     p.xh_tab = reinterpret_cast<const float*>(S->d_blob + S->off_xh);
     p.w_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_w);
-    p.rt_tab = reinterpret_cast<const float*>(S->d_blob + S->off_rt);
+    p.rt_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_rt);
     p.n_prims = (int)S->dprims.size();
     p.n_geoms = (int)S->dgeoms.size();
     p.n_pairs = (int)S->dpairs.size();
@@ -618,7 +619,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     if (T->hist_A && S->grid.n_abins == 0) return fail(SPUT_ERR_INVALID_ARG, "hist_A requested but n_abins = 0");
     unsigned long long tb = opts->ticket_begin, te = opts->ticket_end ? opts->ticket_end : S->n_tickets;
     if (tb > te || te > S->n_tickets) return fail(SPUT_ERR_INVALID_ARG, "ticket range outside [0, n_tickets]");
-    int threads = opts->block_threads ? opts->block_threads : 128;
+    int threads = opts->block_threads ? opts->block_threads : 192;
     if (threads < 32 || threads > 256 || threads % 32) return fail(SPUT_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
     int chunk = opts->ticket_chunk ? opts->ticket_chunk : 32;
     if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
@@ -809,7 +810,7 @@ sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* str
     stats->attempts = h[6];
     stats->device_status = (uint32_t)(h[1 + kNumStats] & 0xffffffffu);
     stats->grid_blocks = 0;
-    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : 128);
+    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : 192);
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, S->ev0, S->ev1);
     stats->kernel_ms = ms;

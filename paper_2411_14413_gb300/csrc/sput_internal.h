@@ -49,19 +49,15 @@ struct alignas(16) DevGeom {
 
 struct alignas(16) DevCathode {
     float c[3], n[3], e1[3], e2[3];
-    // racetrack: radial pdf ~ r exp(-z^2), z = (r - r0) k, k = 1/(sigma sqrt 2), on [0, R].
-    // Mass below r:  L(r) = A (C0 - e^{-z^2}) + B (erf z + erf z0)   [z0 = r0 k]
-    // Mass above r:  U(r) = A (e^{-z^2} - CR) + B (erfc z - erfc zR) [zR = (R - r0) k]
-    // with A = sigma^2, B = r0 sigma sqrt(pi/2); FR = L(R).
-    float rt_r0, rt_R, rt_FR, rt_A;
-    float rt_B, rt_C0, rt_k, rt_E0;        // rt_C0 = e^{-z0^2}, rt_E0 = erf z0
-    float rt_Ec0, rt_CR, rt_EcR, rt_pad;   // erfc z0, e^{-zR^2}, erfc zR
+    // racetrack: inverse radial CDF as cubic pieces, rt_n per half (see rt_tab of Params)
+    float rt_R;
+    float rt_pad[11];
     float coef[6];
     float coef_norm;                       // sum c_i/(i+1)
     int cos_general;                       // 0 = pure cosine (mu = sqrt(u))
     int target;                            // local index of the target disc
     int pair;                              // interaction pair (tables)
-    int rt_tab;                            // offset of this cathode's two racetrack guess tables
+    int rt_tab;                            // float4 offset of this cathode's 2 rt_n racetrack pieces
     int pad0;
     float v_per_sqrtE;                     // speed (km/s) = v_per_sqrtE * sqrt(E / eV)
     float E_per_v2;                        // E (eV) = E_per_v2 * v^2
@@ -105,7 +101,7 @@ struct Params {
     const float4* bm_tab;              // n_bm cubic pieces of b_max/a over ln eps
     const float* xh_tab;               // n_bm + 1 head-on apsis values (linear)
     const float4* w_tab;               // all pairs' K and M pieces
-    const float* rt_tab;               // racetrack guesses
+    const float4* rt_tab;              // racetrack inverse-CDF pieces (2 rt_n per cathode)
     int n_prims, n_geoms, n_pairs, n_inst;
     int n_bm, n_w_total;
     float bm_lo, bm_inv_h;
@@ -115,7 +111,7 @@ struct Params {
     int max_attempts;
     int max_prims;
     long long max_collisions;
-    int rt_n;                          // racetrack guess nodes per cathode - 1
+    int rt_n;                          // racetrack pieces per half
     // grid
     int nx, ny;
     float half_u, half_v, cells_per_mm_u, cells_per_mm_v;

@@ -338,22 +338,29 @@ double racetrack_F64(double r0, double sg, double r)
            r0 * sg * std::sqrt(kPi / 2.0) * (std::erf((r - r0) * k) + std::erf(r0 * k));
 }
 
-void racetrack_guess(double r0, double sg, double R, int n, float* out)
+void racetrack_table(double r0, double sg, double R, int n, float4* out)
 {
-    // out[0..n]: r at u = (j/n)^2; out[n+1..2n+1]: r at u = 1 - (j/n)^2
-    double FR = racetrack_F64(r0, sg, R);
-    for (int half = 0; half < 2; ++half)
-        for (int j = 0; j <= n; ++j) {
-            double q = (double)j / n;
-            q *= q;
-            double u = half ? 1.0 - q : q;
-            double tgt = u * FR, lo = 0.0, hi = R;
-            for (int it = 0; it < 100; ++it) {
-                double m = 0.5 * (lo + hi);
-                if (racetrack_F64(r0, sg, m) < tgt) lo = m;
-                else hi = m;
+    // Inverse of the radial CDF as cubic pieces: n pieces in s = sqrt(u) on
+    // [0, sqrt(1/2)] (lower half), then n pieces in q = sqrt(1-u) on the same
+    // interval (upper half); each piece interpolates four exact inverses.
+    const double FR = racetrack_F64(r0, sg, R), half = std::sqrt(0.5);
+    auto inv = [&](double u) {
+        double tgt = u * FR, lo = 0.0, hi = R;
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * R; ++it) {
+            double m = 0.5 * (lo + hi);
+            if (racetrack_F64(r0, sg, m) < tgt) lo = m;
+            else hi = m;
+        }
+        return 0.5 * (lo + hi);
+    };
+    for (int side = 0; side < 2; ++side)
+        for (int i = 0; i < n; ++i) {
+            double f[4];
+            for (int j = 0; j < 4; ++j) {
+                double x = half * (i + j / 3.0) / n;
+                f[j] = inv(side ? 1.0 - x * x : x * x);
             }
-            out[half * (n + 1) + j] = (float)(0.5 * (lo + hi));
+            out[side * n + i] = cubic_from_thirds(f[0], f[1], f[2], f[3]);
         }
 }
 

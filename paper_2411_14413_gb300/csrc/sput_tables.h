@@ -67,8 +67,8 @@ double K64(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_therma
 double M64(const PairPhys& pp, const BmaxTable* bt, double s_gas, double v, int monotone);
 int h_monotone(const PairPhys& pp, const BmaxTable* bt, double g_top);
 
-// Racetrack inverse-CDF guesses: n+1 values at u = (j/n)^2, then n+1 at u = 1 - (j/n)^2.
-void racetrack_guess(double r0, double sigma, double R, int n, float* out);
+// Racetrack inverse CDF: n cubic pieces in sqrt(u), then n in sqrt(1-u), over [0, sqrt(1/2)].
+void racetrack_table(double r0, double sigma, double R, int n, float4* out);
 double racetrack_F64(double r0, double sigma, double r);
 
 // Cubic through f(0), f(1/3), f(2/3), f(1) on t in [0,1].

@@ -174,39 +174,17 @@ struct Lane {
     unsigned long long ticket;
 };
 
-__device__ float racetrack_r(const DevCathode& C, const float* rt_tab, int rt_n, float u)
+__device__ __forceinline__ float racetrack_r(const DevCathode& C, const float4* rt_tab, int rt_n, float u)
 {
-    // Invert the radial CDF: guess from a table in sqrt(u) (lower half) or
-    // sqrt(1-u) (upper half), then Newton on the log of the lower or upper
-    // mass, both written without cancellation (erfc in the tails).
+    // inverse radial CDF: cubic pieces in sqrt(u) below the median, in
+    // sqrt(1-u) above it (1 - u is exact for RN = m 2^-24)
     const bool upper = u > 0.5f;
-    const float q = upper ? 1.0f - u : u;  // exact for RN = m 2^-24
-    if (q <= 0.0f) return C.rt_R;
-    float x = sqrtf(q) * (float)rt_n;
-    int j = min((int)x, rt_n - 1);
-    float f = x - (float)j;
-    const float* g = rt_tab + C.rt_tab + (upper ? rt_n + 1 : 0);
-    float r = fmaf(f, g[j + 1] - g[j], g[j]);
-    const float lt = logf(q * C.rt_FR);
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-        const float z = (r - C.rt_r0) * C.rt_k;
-        const float e = expf(-z * z);
-        const float pdf = r * e;
-        float mass, dlog;
-        if (!upper) {
-            const float t2 = z <= 0.0f ? erfcf(-z) - C.rt_Ec0 : erff(z) + C.rt_E0;
-            mass = fmaf(C.rt_A, C.rt_C0 - e, C.rt_B * t2);
-            dlog = pdf / mass;
-        } else {
-            mass = fmaf(C.rt_A, e - C.rt_CR, C.rt_B * (erfcf(z) - C.rt_EcR));
-            dlog = -pdf / mass;
-        }
-        if (!(mass > 0.0f) || !(pdf > 0.0f)) break;
-        r -= (logf(mass) - lt) / dlog;
-        r = fminf(fmaxf(r, 0.0f), C.rt_R);
-    }
-    return r;
+    const float q = upper ? 1.0f - u : u;
+    const float x = sqrtf(q) * ((float)rt_n * 1.41421356237309515f);
+    const int i = min((int)x, rt_n - 1);
+    const float t = x - (float)i;
+    const float4 c = rt_tab[C.rt_tab + (upper ? rt_n : 0) + i];
+    return fminf(fmaxf(fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x), 0.0f), C.rt_R);
 }
 
 __device__ float cosine_sum_mu(const DevCathode& C, float u)
@@ -230,7 +208,7 @@ __device__ float cosine_sum_mu(const DevCathode& C, float u)
     return 0.5f * (lo + hi);
 }
 
-__device__ void launch_state(const Params& P, const float* rt_tab, uint32_t inst, uint32_t pid, float& px,
+__device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t inst, uint32_t pid, float& px,
                              float& py, float& pz, float& dx, float& dy, float& dz, float& E)
 {
     const DevInstance& I = P.inst[inst];
@@ -331,7 +309,7 @@ __device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, u
 }
 
 // ------------------------------------------------------------- one flight
-enum { kStepCollided = 0, kStepLanded = 1, kStepTimedOut = 2 };
+enum { kStepNone = -1, kStepCollided = 0, kStepLanded = 1, kStepTimedOut = 2 };
 
 struct StepOut {
     float t;        // landing: distance to the hit; otherwise the flight length
@@ -340,17 +318,18 @@ struct StepOut {
     int nonfinite;  // the state became NaN/Inf
 };
 
-// Flight k+1 of the atom in S: free path, surface test, then either the
-// landing (S keeps the pre-flight position; out.t is the hit distance) or the
-// move to the collision point and the binary collision with a gas atom.
-__device__ int flight_step(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
-                           StepOut& out)
+// Free flight k+1 of the atom in S and the surface test.  Landing: S keeps the
+// pre-flight position and out.t is the hit distance.  Otherwise the atom moves
+// to the collision point; w is the flight's Philox block (impact parameter,
+// azimuth and first acceptance word are used by the collision).
+__device__ int flight_move(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
+                           StepOut& out, uint4& w)
 {
     S.k += 1u;
     out.attempts = 0;
     out.nonfinite = 0;
     out.prim = -1;
-    const uint4 w = philox(P.key0, P.key1, S.pid, S.inst, S.k, 0u);
+    w = philox(P.key0, P.key1, S.pid, S.inst, S.k, 0u);
     const DevPair pr = pairs[S.pair];
     // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
     const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
@@ -376,8 +355,6 @@ __device__ int flight_step(Lane& S, const Params& P, const TableView& T, const D
         out.prim = hb;
         return kStepLanded;
     }
-
-    // move, then collide
     out.t = ell;
     S.px = fmaf(ell, S.dx, S.px);
     S.py = fmaf(ell, S.dy, S.py);
@@ -388,39 +365,112 @@ __device__ int flight_step(Lane& S, const Params& P, const TableView& T, const D
         return kStepTimedOut;
     }
     if ((long long)S.k > P.max_collisions) return kStepTimedOut;
+    return kStepCollided;
+}
 
-    const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
-    float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
-    if (P.gas_thermal) {
-        // gas partner: Maxwellian weighted by sigma(g) g, rejection against M(v)
-        const float M = wtab_eval(T, pr, pr.M_off, S.speed);
-        uint4 wa = make_uint4(0u, 0u, 0u, 0u);
-        for (int a = 0; a < P.max_attempts; ++a) {
-            const uint4 wn = philox(P.key0, P.key1, S.pid, S.inst, S.k, 1u + (uint32_t)a);
+// position of the n-th (0-based) set bit of mask; mask has more than n set bits
+__device__ __forceinline__ int nth_set_bit(unsigned mask, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1)
+        if (__popc(mask & ((1u << (pos + w)) - 1u)) <= n) pos += w;
+    return pos;
+}
+
+// Gas partners of every lane with `need`, drawn by the whole warp: the
+// Maxwellian weighted by sigma(g) g by rejection against M(v), attempt a of a
+// particle from its own Philox block (1 + a) and acceptance word, the first
+// accepted attempt kept (attempt A-1 if none is).  Each round spreads the
+// pending particles' next attempts over all 32 lanes (m consecutive attempts
+// per particle), so the result is the sequential rejection loop's result while
+// the lanes stay busy.  Must be called by all 32 lanes together.
+__device__ void partner_sample_warp(bool need, const Params& P, const TableView& T, const DevPair* pairs,
+                                    uint32_t pid, uint32_t inst, uint32_t k, int pair, float vx, float vy, float vz,
+                                    float M, uint32_t acc0, float& Vx, float& Vy, float& Vz, int& attempts)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int A = P.max_attempts;
+    unsigned pending = __ballot_sync(kFull, need);
+    int next_a = 0;
+    Vx = Vy = Vz = 0.0f;
+    attempts = 0;
+    while (pending) {
+        const int np = __popc(pending);
+        const int m = 32 / np;
+        const int slot = lane / m, j = lane - slot * m;
+        const bool has_job = slot < np;
+        const int owner = has_job ? nth_set_bit(pending, slot) : lane;
+        const uint32_t o_pid = __shfl_sync(kFull, pid, owner);
+        const uint32_t o_inst = __shfl_sync(kFull, inst, owner);
+        const uint32_t o_k = __shfl_sync(kFull, k, owner);
+        const int o_pair = __shfl_sync(kFull, pair, owner);
+        const float o_vx = __shfl_sync(kFull, vx, owner);
+        const float o_vy = __shfl_sync(kFull, vy, owner);
+        const float o_vz = __shfl_sync(kFull, vz, owner);
+        const float o_M = __shfl_sync(kFull, M, owner);
+        const uint32_t o_acc0 = __shfl_sync(kFull, acc0, owner);
+        const int o_next = __shfl_sync(kFull, next_a, owner);
+        const int a = o_next + j;
+        bool acc = false;
+        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+        if (has_job && a < A) {
+            const uint4 wn = philox(P.key0, P.key1, o_pid, o_inst, o_k, 1u + (uint32_t)a);
             const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
             const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
             float s1, c1;
             sincospif(2.0f * rn(wn.y), &s1, &c1);
             const float c3 = cospif(2.0f * rn(wn.w));
-            Vx = P.s_gas * R0 * c1;
-            Vy = P.s_gas * R0 * s1;
-            Vz = P.s_gas * R1 * c3;
+            cx = P.s_gas * R0 * c1;
+            cy = P.s_gas * R0 * s1;
+            cz = P.s_gas * R1 * c3;
             float ua;
-            if (a == 0) ua = rn(w.w);
-            else {
+            if (a == 0) {
+                ua = rn(o_acc0);
+            } else {
+                const uint4 wa =
+                    philox(P.key0, P.key1, o_pid, o_inst, o_k, 1u + (uint32_t)A + (uint32_t)((a - 1) >> 2));
                 const int q = (a - 1) & 3;
-                if (q == 0)
-                    wa = philox(P.key0, P.key1, S.pid, S.inst, S.k,
-                                1u + (uint32_t)P.max_attempts + (uint32_t)((a - 1) >> 2));
                 ua = rn(q == 0 ? wa.x : (q == 1 ? wa.y : (q == 2 ? wa.z : wa.w)));
             }
-            const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
+            const float gx = o_vx - cx, gy = o_vy - cy, gz = o_vz - cz;
             const float g2 = gx * gx + gy * gy + gz * gz;
-            ++out.attempts;
-            if (ua * M <= h_of_g(T, pr, sqrtf(g2), g2)) break;
+            acc = ua * o_M <= h_of_g(T, pairs[o_pair], sqrtf(g2), g2) || a == A - 1;
         }
+        const unsigned accm = __ballot_sync(kFull, acc);
+        const bool is_owner = (pending >> lane) & 1u;
+        int src = lane, first = 0;
+        bool done = false;
+        if (is_owner) {
+            const int my_slot = __popc(pending & lt);
+            const unsigned range = (m >= 32 ? kFull : ((1u << m) - 1u)) << (my_slot * m);
+            const unsigned hit = accm & range;
+            if (hit) {
+                src = __ffs(hit) - 1;
+                first = src - my_slot * m;
+                done = true;
+            }
+        }
+        const float sx = __shfl_sync(kFull, cx, src);
+        const float sy = __shfl_sync(kFull, cy, src);
+        const float sz = __shfl_sync(kFull, cz, src);
+        if (done) {
+            Vx = sx;
+            Vy = sy;
+            Vz = sz;
+            attempts = next_a + first + 1;
+        } else if (is_owner) {
+            next_a += m;
+        }
+        pending &= ~__ballot_sync(kFull, done);
     }
-    // binary collision in the CM frame: rotate g = v - V by (chi, psi), |g| kept
+}
+
+// Binary collision in the CM frame: rotate g = v - V by (chi, psi), |g| kept.
+__device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevPair& pr, float vx, float vy, float vz,
+                        float Vx, float Vy, float Vz, const uint4& w)
+{
     const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
     const float g2 = gx * gx + gy * gy + gz * gz;
     if (g2 > 0.0f) {
@@ -455,7 +505,29 @@ __device__ int flight_step(Lane& S, const Params& P, const TableView& T, const D
         S.dz = nvz * is;
     }
     ++S.ncoll;
-    return kStepCollided;
+}
+
+// One flight of every active lane of the warp (flight, surface test, then for
+// the lanes that collide: warp-wide partner sampling and the scattering).
+// Must be called by all 32 lanes together; inactive lanes return kStepNone.
+__device__ int flight_step_warp(bool active, Lane& S, const Params& P, const TableView& T, const DevPrim* prims,
+                                const DevPair* pairs, StepOut& out)
+{
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    int res = kStepNone;
+    out.attempts = 0;
+    if (active) res = flight_move(S, P, T, prims, pairs, out, w);
+    const bool coll = res == kStepCollided;
+    const DevPair pr = pairs[S.pair];
+    const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
+    float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
+    if (P.gas_thermal) {
+        const float M = coll ? wtab_eval(T, pr, pr.M_off, S.speed) : 0.0f;
+        partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, M, w.w, Vx, Vy, Vz,
+                            out.attempts);
+    }
+    if (coll) scatter(S, P, T, pr, vx, vy, vz, Vx, Vy, Vz, w);
+    return res;
 }
 
 // ------------------------------------------------------------- kernel
@@ -586,12 +658,11 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params P)
             }
         }
         if (!__any_sync(kFull, alive)) break;
-        if (!alive) continue;
 
-        // ---------------------------------------------------- one flight
-        ++c_flights;
+        // ---------------------------------------------------- one flight (all lanes together)
         StepOut so;
-        const int res = flight_step(S, P, T, s_prims, s_pairs, so);
+        const int res = flight_step_warp(alive, S, P, T, s_prims, s_pairs, so);
+        if (alive) ++c_flights;
         c_att += so.attempts;
         if (res == kStepLanded) {
             // ------------------------------------------------ landing tally
@@ -668,7 +739,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params P)
             ++c_timed;
             ++c_particles;
             alive = false;
-        } else {
+        } else if (res == kStepCollided) {
             ++c_coll;
         }
     }
@@ -702,7 +773,6 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params P)
 __global__ void probe_kernel(const Params P, int what, int idx, int n, const double* x, double* y)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     TableView T;
     T.bm = P.bm_tab;
     T.xh = P.xh_tab;
@@ -711,6 +781,45 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
     T.n_bm = P.n_bm;
     T.bm_lo = P.bm_lo;
     T.bm_inv_h = P.bm_inv_h;
+    if (what == SPUT_PROBE_TRACE) {
+        // state after each flight of particle x[i] of instance idx, kTraceRows rows of 10;
+        // the flight step is warp-collective, so lanes past n take part without a particle
+        const bool valid = i < n;
+        Lane S;
+        S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = 0.0f;
+        S.pid = S.inst = S.k = S.ncoll = 0u;
+        S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
+        S.ng14 = S.E_per_v2 = 0.0f;
+        S.ticket = 0ull;
+        double* o = valid ? y + (size_t)i * kTraceRows * 10 : nullptr;
+        if (valid) {
+            start_particle(S, P, P.geoms, (uint32_t)idx, (uint32_t)x[i], 0ull);
+            for (int r = 0; r < kTraceRows * 10; ++r) o[r] = 0.0;
+            for (int r = 1; r < kTraceRows; ++r) o[r * 10 + 7] = -2.0;
+            o[0] = S.px; o[1] = S.py; o[2] = S.pz; o[3] = S.dx; o[4] = S.dy; o[5] = S.dz; o[6] = S.speed;
+            o[7] = -1.0;
+        }
+        bool running = valid;
+        for (int r = 1; r < kTraceRows; ++r) {
+            if (!__any_sync(kFull, running)) break;
+            StepOut so;
+            const int status = flight_step_warp(running, S, P, T, P.prims, P.pairs, so);
+            if (running) {
+                double* q = o + (size_t)r * 10;
+                float px = S.px, py = S.py, pz = S.pz;
+                if (status == kStepLanded) {
+                    px = fmaf(so.t, S.dx, S.px);
+                    py = fmaf(so.t, S.dy, S.py);
+                    pz = fmaf(so.t, S.dz, S.pz);
+                }
+                q[0] = px; q[1] = py; q[2] = pz; q[3] = S.dx; q[4] = S.dy; q[5] = S.dz; q[6] = S.speed;
+                q[7] = status; q[8] = status == kStepLanded ? so.prim : so.attempts; q[9] = so.t;
+                if (status != kStepCollided) running = false;
+            }
+        }
+        return;
+    }
+    if (i >= n) return;
     if (what == SPUT_PROBE_CHI) {
         const float eps = (float)x[2 * i], beta = (float)x[2 * i + 1];
         const float le = logf(eps);
@@ -723,31 +832,6 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         float val = wtab_eval(T, pr, what == SPUT_PROBE_K ? pr.K_off : pr.M_off, v);
         if (what == SPUT_PROBE_K && !P.gas_thermal) val *= v;  // the table holds sigma(v) = K/v
         y[i] = val;
-    } else if (what == SPUT_PROBE_TRACE) {
-        // state after each flight of particle x[i] of instance idx, kTraceRows rows of 10
-        Lane S;
-        start_particle(S, P, P.geoms, (uint32_t)idx, (uint32_t)x[i], 0ull);
-        double* o = y + (size_t)i * kTraceRows * 10;
-        for (int r = 0; r < kTraceRows * 10; ++r) o[r] = 0.0;
-        o[0] = S.px; o[1] = S.py; o[2] = S.pz; o[3] = S.dx; o[4] = S.dy; o[5] = S.dz; o[6] = S.speed; o[7] = -1.0;
-        int status = kStepCollided;
-        for (int r = 1; r < kTraceRows; ++r) {
-            double* q = o + (size_t)r * 10;
-            if (status != kStepCollided) {
-                q[7] = -2.0;
-                continue;
-            }
-            StepOut so;
-            status = flight_step(S, P, T, P.prims, P.pairs, so);
-            float px = S.px, py = S.py, pz = S.pz;
-            if (status == kStepLanded) {
-                px = fmaf(so.t, S.dx, S.px);
-                py = fmaf(so.t, S.dy, S.py);
-                pz = fmaf(so.t, S.dz, S.pz);
-            }
-            q[0] = px; q[1] = py; q[2] = pz; q[3] = S.dx; q[4] = S.dy; q[5] = S.dz; q[6] = S.speed;
-            q[7] = status; q[8] = status == kStepLanded ? so.prim : so.attempts; q[9] = so.t;
-        }
     } else if (what == SPUT_PROBE_LAUNCH) {
         float px, py, pz, dx, dy, dz, E;
         launch_state(P, P.rt_tab, (uint32_t)idx, (uint32_t)x[i], px, py, pz, dx, dy, dz, E);
