@@ -214,7 +214,7 @@ typedef struct sput_run_opts {
     uint64_t seed;
     uint64_t ticket_begin, ticket_end; /* run tickets [begin, end); end = 0 means all */
     int accumulate;              /* 0: zero the requested tallies first; 1: add into them */
-    int block_threads;           /* 0 = default (192); else a multiple of 32 in [32, 256] */
+    int block_threads;           /* 0 = default (256); else a multiple of 32 in [32, 256] */
     int blocks_per_sm;           /* 0 = default (occupancy limit) */
     int ticket_chunk;            /* tickets a warp takes per refill; 0 = default (32) */
     int timeout_ms;              /* host wait limit when stats are requested; 0 = none */

@@ -316,6 +316,15 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         D.ny = (float)n[1];
         D.nz = (float)n[2];
         D.p0sq = (float)(P.p0 * P.p0);
+        // bounding sphere about the centre
+        double br = 0.0;
+        if (P.kind == SPUT_PRIM_RECT) br = std::sqrt(P.p0 * P.p0 + P.p1 * P.p1);
+        else if (P.kind == SPUT_PRIM_DISC) br = P.p1;
+        else if (P.kind == SPUT_PRIM_CYLINDER) br = std::sqrt(P.p0 * P.p0 + P.p1 * P.p1);
+        D.bx = D.cx;
+        D.by = D.cy;
+        D.bz = D.cz;
+        D.br = (float)(br * (1.0 + 1e-6));
     }
     S->dgeoms.resize(S->geoms.size());
     S->max_prims = 0;
@@ -619,7 +628,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     if (T->hist_A && S->grid.n_abins == 0) return fail(SPUT_ERR_INVALID_ARG, "hist_A requested but n_abins = 0");
     unsigned long long tb = opts->ticket_begin, te = opts->ticket_end ? opts->ticket_end : S->n_tickets;
     if (tb > te || te > S->n_tickets) return fail(SPUT_ERR_INVALID_ARG, "ticket range outside [0, n_tickets]");
-    int threads = opts->block_threads ? opts->block_threads : 192;
+    int threads = opts->block_threads ? opts->block_threads : 256;
     if (threads < 32 || threads > 256 || threads % 32) return fail(SPUT_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
     int chunk = opts->ticket_chunk ? opts->ticket_chunk : 32;
     if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
@@ -810,7 +819,7 @@ sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* str
     stats->attempts = h[6];
     stats->device_status = (uint32_t)(h[1 + kNumStats] & 0xffffffffu);
     stats->grid_blocks = 0;
-    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : 192);
+    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : 256);
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, S->ev0, S->ev1);
     stats->kernel_ms = ms;

@@ -31,7 +31,7 @@ enum : uint32_t {
     kStatusBadIndex = 1u << 1,    // a tally or table index fell outside its buffer; the write was skipped
 };
 
-// One primitive, 64 bytes; n = u x v precomputed.
+// One primitive, 80 bytes; n = u x v precomputed; (bx, by, bz, br) bounds it.
 struct alignas(16) DevPrim {
     float cx, cy, cz;
     int kind;
@@ -41,6 +41,7 @@ struct alignas(16) DevPrim {
     float p1;
     float nx, ny, nz;
     float p0sq;  // disc: inner radius^2; cylinder: radius^2
+    float bx, by, bz, br;  // bounding sphere (centre, radius); unused for the box
 };
 
 struct alignas(16) DevGeom {

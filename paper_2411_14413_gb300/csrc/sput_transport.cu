@@ -123,9 +123,16 @@ __device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
     const float ie = 1.0f / eps;
     const float b2 = beta * beta;
     float x = fmaxf(beta, xh);
+    // Terms of Phi with d_i = 1.2 and 6.0 are dropped, lane by lane, where their
+    // share of the potential is below 1e-8: c_i d_i e^{-d_i x} < 1e-8 c_0 d_0 e^{-d_0 x}
+    // for x > 23 (d = 1.2) and x > 4 (d = 6.0).  Both x-bounds hold from the start
+    // of the apsis iteration onwards because x only grows from max(beta, x_h).
+    const bool t1 = x < 23.0f, t2 = x < 4.0f;
 #pragma unroll
     for (int it = 0; it < kApsisIters; ++it) {
-        float e0 = kMolC0 * expf(-kMolD0 * x), e1 = kMolC1 * expf(-kMolD1 * x), e2 = kMolC2 * expf(-kMolD2 * x);
+        float e0 = kMolC0 * expf(-kMolD0 * x);
+        float e1 = t1 ? kMolC1 * expf(-kMolD1 * x) : 0.0f;
+        float e2 = t2 ? kMolC2 * expf(-kMolD2 * x) : 0.0f;
         float ph = e0 + e1 + e2;
         float dph = -(kMolD0 * e0 + kMolD1 * e1 + kMolD2 * e2);
         float ix = 1.0f / x;
@@ -138,17 +145,18 @@ __device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
     const float bt = beta / x0;
     const float bt2 = bt * bt;
     const float iex = ie / x0;
+    const bool u1 = x0 < 23.0f, u2 = x0 < 4.0f;
     const float p0 = kMolC0 * expf(-kMolD0 * x0) * iex;
-    const float p1 = kMolC1 * expf(-kMolD1 * x0) * iex;
-    const float p2 = kMolC2 * expf(-kMolD2 * x0) * iex;
+    const float p1 = u1 ? kMolC1 * expf(-kMolD1 * x0) * iex : 0.0f;
+    const float p2 = u2 ? kMolC2 * expf(-kMolD2 * x0) * iex : 0.0f;
     const float y0 = kMolD0 * x0, y1 = kMolD1 * x0, y2 = kMolD2 * x0;
     float s = 0.0f;
 #pragma unroll 4
     for (int j = 0; j < kGMHalf; ++j) {
         const float4 nd = gm[j];  // (u, 1/(1+u), u/(1-u^2), 1/u - 1)
         float D = p0 * fmaf(nd.z, one_minus_exp_neg(y0 * nd.w), nd.y);
-        D = fmaf(p1, fmaf(nd.z, one_minus_exp_neg(y1 * nd.w), nd.y), D);
-        D = fmaf(p2, fmaf(nd.z, one_minus_exp_neg(y2 * nd.w), nd.y), D);
+        if (u1) D = fmaf(p1, fmaf(nd.z, one_minus_exp_neg(y1 * nd.w), nd.y), D);
+        if (u2) D = fmaf(p2, fmaf(nd.z, one_minus_exp_neg(y2 * nd.w), nd.y), D);
         float S = sqrtf(bt2 + D);
         s += D / (S * (S + bt));
     }
@@ -343,7 +351,15 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     const int excl = S.k == 1u ? S.target : -1;
     for (int li = 0; li < S.gcount; ++li) {
         if (li == excl) continue;
-        const float t = hit_prim(prims[S.gbegin + li], P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
+        const DevPrim& Q = prims[S.gbegin + li];
+        // skip a primitive whose bounding sphere lies beyond min(ell, best t): no
+        // hit on it can be the landing (margin covers FP32 rounding)
+        if (Q.kind != SPUT_PRIM_BOX) {
+            const float ex = Q.bx - S.px, ey = Q.by - S.py, ez = Q.bz - S.pz;
+            const float reach = fminf(ell, tb) * 1.0001f + Q.br + 1e-3f;
+            if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
+        }
+        const float t = hit_prim(Q, P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
         if (t < tb) {
             tb = t;
             hb = li;
@@ -572,7 +588,7 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
 }
 
 template <bool kCount64>
-__global__ void __launch_bounds__(256) transport_kernel(const Params P)
+__global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout L = smem_layout(P);
