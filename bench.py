@@ -35,8 +35,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-collisions/sec and landed particles/sec on 1 GB300 vs oracle; roofline fraction"
 UNIT = "collisions/s"
-WORKLOAD = ("quaternary co-sputter Ni/Pd/Pt/Ru, 4 cathodes tilted 30 deg confocal at 120 mm, "
-            "4 x 1e7 particles, Ar 0.5 Pa 300 K, E_i 400 eV, 100 mm wafer, 200x200 int64 counts + fp64 energy")
+WORKLOADS = {
+    "quaternary": ("quaternary co-sputter Ni/Pd/Pt/Ru, 4 cathodes tilted 30 deg confocal at 120 mm, "
+                   "4 x 1e7 particles, Ar 0.5 Pa 300 K, E_i 400 eV, 100 mm wafer, 200x200 int64 counts + fp64 energy"),
+    "sweep": ("batched sweep: 4 cathodes x 16 pressures (0.2-2 Pa log) x 8 tilts (0-40 deg) = 512 instances, "
+              "particle counts uniform in [1e5, 1e7] (seed 0), one launch, autotuned launch shape, "
+              "100x100 int64 counts per instance"),
+    "large": ("large: single Ni cathode, Ar 3 Pa, 64 primitives (57 shields), 512x512 int64 counts + fp64 energy "
+              "+ 64-bin energy + 32-bin angle histograms"),
+}
+WORKLOAD = WORKLOADS["quaternary"]
 # Algorithmic work per collision: active-lane instructions per collision of the
 # reference capture of the transport kernel on this workload (ncu
 # smsp__thread_inst_executed.sum / collisions of the launch, quaternary scene
@@ -121,14 +129,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- reference arm
-def cpu_oracle_rate(n_per_cathode, n_threads=None):
+def sample_scene(workload, n_per_instance):
+    """A bounded sample of the workload: every instance with n_per_instance particles."""
+    import workloads
+
+    if workload == "quaternary":
+        return workloads.scene_quaternary(n_per_cathode=n_per_instance)
+    if workload == "sweep":
+        return workloads.scene_tilt_pressure_sweep().with_particles(n_per_instance)
+    return workloads.scene_large_shielded(n=n_per_instance)
+
+
+def cpu_oracle_rate(n_per_instance, n_threads=None, workload="quaternary"):
     """Oracle collisions/s and landed/s on a bounded sample of the workload."""
     import numpy as np
 
     import oracle
-    import workloads
 
-    sc = workloads.scene_quaternary(n_per_cathode=n_per_cathode)
+    sc = sample_scene(workload, n_per_instance)
     o = oracle.OracleScene(sc)
     n_threads = n_threads or (os.cpu_count() or 1)
     t0 = time.perf_counter()
@@ -137,7 +155,7 @@ def cpu_oracle_rate(n_per_cathode, n_threads=None):
     coll = int(out["ncoll"].sum())
     landed = int(np.sum(out["prim"] >= 0))
     return {"collisions": coll, "landed": landed, "seconds": dt, "cores": n_threads,
-            "particles": sc.total_particles}
+            "particles": sc.total_particles, "instances": len(sc.instances)}
 
 
 def run_reference(args, rank):
@@ -147,24 +165,28 @@ def run_reference(args, rank):
 
     oracle.build()
     n_per = args.ref_particles
+    if args.workload == "sweep":
+        n_per = max(1, n_per // 128)
     for _ in range(args.warmup):
-        cpu_oracle_rate(max(1, n_per // 8))
+        cpu_oracle_rate(max(1, n_per // 8), workload=args.workload)
     tot_c = tot_l = tot_t = 0.0
     cores = 0
+    nparts = 0
     for _ in range(args.steps):
-        r = cpu_oracle_rate(n_per)
+        r = cpu_oracle_rate(n_per, workload=args.workload)
+        nparts = r["particles"]
         tot_c += r["collisions"]
         tot_l += r["landed"]
         tot_t += r["seconds"]
         cores = r["cores"]
     value = tot_c / tot_t
-    sample = f"{4 * n_per} particles ({n_per} per cathode) of the workload per step, all host cores"
+    sample = f"{nparts} particles ({n_per} per instance) of the workload per step, all host cores"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "landed_per_s": tot_l / tot_t,
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": {"workload": WORKLOADS[args.workload], "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -190,15 +212,28 @@ def run_ours(args, rank, world, local_rank):
     # CPU baseline first (rank 0, N = 1 only), before the GPU work starts
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = cpu_oracle_rate(args.cpu_particles)
+        n_cpu = args.cpu_particles if args.workload != "sweep" else max(1, args.cpu_particles // 128)
+        r = cpu_oracle_rate(n_cpu, workload=args.workload)
         cpu = {"value": r["collisions"] / r["seconds"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-               "sample": f"{r['particles']} particles ({args.cpu_particles} per cathode) of the workload, "
+               "sample": f"{r['particles']} particles ({n_cpu} per instance) of the workload, "
                          f"{r['seconds']:.1f} s wall on {r['cores']} threads",
                "landed_per_s": r["landed"] / r["seconds"]}
         log("cpu baseline:", cpu)
 
-    sc = workloads.scene_quaternary(n_per_cathode=args.particles)
-    tr = pkg.Transport(sc, device=local_rank, energy=True)
+    if args.workload == "quaternary":
+        sc = workloads.scene_quaternary(n_per_cathode=args.particles)
+    elif args.workload == "sweep":
+        sc = workloads.scene_tilt_pressure_sweep()
+        if args.particles != 10_000_000:
+            sc = sc.with_particles([max(1, int(i["n"] * args.particles / 10_000_000)) for i in sc.instances])
+    else:
+        sc = workloads.scene_large_shielded(n=args.particles * 100)
+    tr = pkg.Transport(sc, device=local_rank, energy=sc.grid["energy"])
+    tune = None
+    if args.workload == "sweep" or args.autotune:
+        tune = tr.autotune(sample_tickets=min(20_000_000, sc.total_particles))
+        log("autotune:", {k: getattr(tune, k) for k in ("block_threads", "blocks_per_sm", "ticket_chunk",
+                                                          "flags", "best_rate")})
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
     seed0 = 1000 * rank
@@ -229,13 +264,33 @@ def run_ours(args, rank, world, local_rank):
     landed = sum(s["landed"] for s in stats)
     kernel_ms = [s["kernel_ms"] for s in stats]
 
+    # plain form: one launch per instance (identical tallies), timed the same way
+    plain = None
+    if args.workload == "sweep" and not args.no_plain:
+        torch.cuda.synchronize(dev)
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        pe0.record(stream)
+        off = 0
+        for i, inst in enumerate(sc.instances):
+            tr.run(seed=seed0, stream=stream.cuda_stream, want_stats=False, ticket_begin=off,
+                   ticket_end=off + inst["n"], accumulate=i > 0)
+            off += inst["n"]
+        pe1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms = pe0.elapsed_time(pe1)
+        plain = {"launches": len(sc.instances), "ms": plain_ms,
+                 "value": stats[0]["collisions"] / (plain_ms / 1e3), "unit": UNIT,
+                 "note": "same seed and tickets as step 0; tallies identical to the batched launch"}
+
     # e2e through the host-buffer entry point: instance table H2D + tallies D2H each step
     L = tr.layout
     pin = lambda shape, dt: torch.zeros(shape, dtype=dt, pin_memory=True)
-    host = {"counts": pin((L.n_instances, L.ny, L.nx), torch.int64),
-            "energy": pin((L.n_instances, L.ny, L.nx), torch.float64),
+    host = {"counts": pin((L.n_instances, L.ny, L.nx), torch.int64 if L.count_type == 1 else torch.int32),
             "prim_counts": pin((L.n_instances, L.max_prims), torch.int64),
             "timed_out": pin((L.n_instances,), torch.int64)}
+    if "energy" in tr.t:
+        host["energy"] = pin((L.n_instances, L.ny, L.nx), torch.float64)
     ht = N.sput_tallies()
     for k2, v in host.items():
         setattr(ht, k2, v.data_ptr())
@@ -287,7 +342,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "landed_per_s": landed_all / (total_ms_all / 1e3),
-        "config": {"workload": WORKLOAD, "particles_per_step_per_gpu": sc.total_particles,
+        "config": {"workload": WORKLOADS[args.workload], "particles_per_step_per_gpu": sc.total_particles,
                    "instances": len(sc.instances), "grid": f"{sc.grid['nx']}x{sc.grid['ny']}",
                    "tallies": "int64 counts + fp64 energy + int64 per-primitive landings",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
@@ -300,6 +355,10 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": (e2e_coll_all / e2e_t_all) if e2e_t_all > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
+        "autotune": None if tune is None else {"block_threads": tune.block_threads, "blocks_per_sm": tune.blocks_per_sm,
+                                               "ticket_chunk": tune.ticket_chunk, "flags": tune.flags,
+                                               "candidates": tune.n_candidates},
+        "plain_per_instance": plain,
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons"),
                    "samples": clk.get("samples"), "power_w_max": clk.get("power_w_max")},
         "step_stats": {"collisions_per_step": coll / args.steps, "landed_per_step": landed / args.steps,
@@ -322,6 +381,9 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=400, help="oracle sample per cathode per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="quaternary")
+    ap.add_argument("--autotune", action="store_true", help="autotune the launch shape before timing")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-launch-per-instance comparison")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -214,12 +214,16 @@ typedef struct sput_run_opts {
     uint64_t seed;
     uint64_t ticket_begin, ticket_end; /* run tickets [begin, end); end = 0 means all */
     int accumulate;              /* 0: zero the requested tallies first; 1: add into them */
-    int block_threads;           /* 0 = default (256); else a multiple of 32 in [32, 256] */
-    int blocks_per_sm;           /* 0 = default (occupancy limit) */
-    int ticket_chunk;            /* tickets a warp takes per refill; 0 = default (32) */
+    int block_threads;           /* 0 = scene default (256, or the autotuned value); else a multiple of 32 in [32, 256] */
+    int blocks_per_sm;           /* 0 = scene default (occupancy limit, or the autotuned value) */
+    int ticket_chunk;            /* tickets a warp takes per refill; 0 = scene default (32, or autotuned) */
     int timeout_ms;              /* host wait limit when stats are requested; 0 = none */
-    int reserved;
+    int flags;                   /* SPUT_RUN_* bits */
 } sput_run_opts;
+
+/* sput_run_opts.flags */
+#define SPUT_RUN_NO_SMEM_COUNTERS 1 /* count landings per primitive with global atomics only */
+#define SPUT_RUN_SMEM_COUNTERS 2    /* privatise them in shared memory (when they fit); default: scene choice */
 
 typedef struct sput_run_stats {
     uint64_t particles;          /* particles that completed (landed or timed out) */
@@ -295,6 +299,38 @@ sput_status sput_run_host(sput_scene* scene, const sput_run_opts* opts, const sp
  * The paper has no counterpart of this entry point. */
 sput_status sput_run_noalloc(sput_scene* scene, const sput_run_opts* opts, void* stream, const sput_tallies* tallies,
                              sput_run_stats* stats);
+
+/* Autotuner: time candidate launch shapes (threads per block, blocks per SM,
+ * ticket chunk, shared-memory counters) on `sample_tickets` tickets taken as
+ * four equal ranges spread over the scene's ticket space, and keep the fastest
+ * (most collisions per second of kernel time) as the scene default for runs
+ * whose opts leave those fields 0.  Uses `tallies` as scratch output (their
+ * contents are overwritten).  Synchronous.  The results of every candidate are
+ * reported in *out. */
+typedef struct sput_tune_result {
+    int block_threads, blocks_per_sm, ticket_chunk, flags; /* the chosen shape */
+    float best_rate;             /* collisions per second of kernel time on the sample */
+    int n_candidates;
+    int reserved;
+    int cand_threads[32], cand_bps[32], cand_chunk[32], cand_flags[32];
+    float cand_rate[32];
+} sput_tune_result;
+
+sput_status sput_autotune(sput_scene* scene, const sput_run_opts* base, void* stream, const sput_tallies* tallies,
+                          uint64_t sample_tickets, sput_tune_result* out);
+
+/* CUDA graph of one run (tally clearing when opts->accumulate == 0, scratch
+ * clearing and the transport kernel), captured on `stream` and instantiated.
+ * sput_graph_launch replays it on `stream` with a new seed (the kernel node's
+ * parameters are updated in the executable graph).  The graph keeps the
+ * tally pointers and ticket range it was made with.  The scene must outlive
+ * the graph; a run or launch of the scene must not overlap another. */
+typedef struct sput_graph sput_graph;
+
+sput_status sput_graph_create(sput_scene* scene, const sput_run_opts* opts, void* stream, const sput_tallies* tallies,
+                              sput_graph** out);
+sput_status sput_graph_launch(sput_graph* graph, uint64_t seed, void* stream);
+void sput_graph_destroy(sput_graph* graph);
 
 /* Free the scene and its device memory. */
 void sput_scene_destroy(sput_scene* scene);

@@ -8,6 +8,10 @@ sm_103a behind the C ABI of ``include/sput.h``; ``api`` is its Python binding.
 from . import _native
 from .api import (
     Transport,
+    sput_autotune,
+    sput_graph_create,
+    sput_graph_destroy,
+    sput_graph_launch,
     run_opts,
     scene_desc,
     sput_instances_set,
@@ -24,6 +28,10 @@ build = _native.build
 
 __all__ = [
     "Transport",
+    "sput_autotune",
+    "sput_graph_create",
+    "sput_graph_destroy",
+    "sput_graph_launch",
     "build",
     "run_opts",
     "scene_desc",

@@ -152,7 +152,7 @@ class sput_tally_layout(C.Structure):
 class sput_run_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("ticket_begin", C.c_uint64), ("ticket_end", C.c_uint64),
                 ("accumulate", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
-                ("ticket_chunk", C.c_int), ("timeout_ms", C.c_int), ("reserved", C.c_int)]
+                ("ticket_chunk", C.c_int), ("timeout_ms", C.c_int), ("flags", C.c_int)]
 
 
 class sput_run_stats(C.Structure):
@@ -165,8 +165,23 @@ class sput_run_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sput_tune_result(C.Structure):
+    _fields_ = [("block_threads", C.c_int), ("blocks_per_sm", C.c_int), ("ticket_chunk", C.c_int),
+                ("flags", C.c_int), ("best_rate", C.c_float), ("n_candidates", C.c_int), ("reserved", C.c_int),
+                ("cand_threads", C.c_int * 32), ("cand_bps", C.c_int * 32), ("cand_chunk", C.c_int * 32),
+                ("cand_flags", C.c_int * 32), ("cand_rate", C.c_float * 32)]
+
+    def candidates(self):
+        return [dict(threads=self.cand_threads[i], bps=self.cand_bps[i], chunk=self.cand_chunk[i],
+                     flags=self.cand_flags[i], rate=self.cand_rate[i]) for i in range(self.n_candidates)]
+
+
+SPUT_RUN_NO_SMEM_COUNTERS = 1
+SPUT_RUN_SMEM_COUNTERS = 2
+
 ABI_STRUCTS = [sput_chamber, sput_primitive, sput_geometry, sput_cathode, sput_instance, sput_grid, sput_physics,
-               sput_scene_desc, sput_record, sput_tallies, sput_tally_layout, sput_run_opts, sput_run_stats]
+               sput_scene_desc, sput_record, sput_tallies, sput_tally_layout, sput_run_opts, sput_run_stats,
+               sput_tune_result]
 
 # name -> (restype, argtypes) for every entry point declared in include/sput.h
 _P = C.c_void_p
@@ -181,6 +196,11 @@ SIGNATURES = {
     "sput_run_host": (C.c_int, [_P, C.POINTER(sput_run_opts), C.POINTER(sput_tallies), C.POINTER(sput_run_stats)]),
     "sput_run_noalloc": (C.c_int, [_P, C.POINTER(sput_run_opts), _P, C.POINTER(sput_tallies), C.POINTER(sput_run_stats)]),
     "sput_scene_destroy": (None, [_P]),
+    "sput_autotune": (C.c_int, [_P, C.POINTER(sput_run_opts), _P, C.POINTER(sput_tallies), C.c_uint64,
+                                C.POINTER(sput_tune_result)]),
+    "sput_graph_create": (C.c_int, [_P, C.POINTER(sput_run_opts), _P, C.POINTER(sput_tallies), C.POINTER(_P)]),
+    "sput_graph_launch": (C.c_int, [_P, C.c_uint64, _P]),
+    "sput_graph_destroy": (None, [_P]),
     "sput_probe": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
 }
 

@@ -151,12 +151,36 @@ def sput_probe(handle, what, idx, x):
 
 
 def run_opts(seed=0, ticket_begin=0, ticket_end=0, accumulate=False, block_threads=0, blocks_per_sm=0,
-             ticket_chunk=0, timeout_ms=0):
+             ticket_chunk=0, timeout_ms=0, flags=0):
     o = N.sput_run_opts()
     o.seed, o.ticket_begin, o.ticket_end = int(seed), int(ticket_begin), int(ticket_end)
     o.accumulate, o.block_threads, o.blocks_per_sm = int(bool(accumulate)), int(block_threads), int(blocks_per_sm)
-    o.ticket_chunk, o.timeout_ms = int(ticket_chunk), int(timeout_ms)
+    o.ticket_chunk, o.timeout_ms, o.flags = int(ticket_chunk), int(timeout_ms), int(flags)
     return o
+
+
+def sput_autotune(handle, opts, stream, tallies, sample_tickets):
+    res = N.sput_tune_result()
+    rc = _lib().sput_autotune(handle, C.byref(opts), C.c_void_p(stream), C.byref(tallies), int(sample_tickets),
+                              C.byref(res))
+    N.check(rc, "sput_autotune")
+    return res
+
+
+def sput_graph_create(handle, opts, stream, tallies):
+    g = C.c_void_p()
+    N.check(_lib().sput_graph_create(handle, C.byref(opts), C.c_void_p(stream), C.byref(tallies), C.byref(g)),
+            "sput_graph_create")
+    return g
+
+
+def sput_graph_launch(graph, seed, stream):
+    N.check(_lib().sput_graph_launch(graph, int(seed), C.c_void_p(stream)), "sput_graph_launch")
+
+
+def sput_graph_destroy(graph):
+    if graph:
+        _lib().sput_graph_destroy(graph)
 
 
 # ------------------------------------------------------------ convenience
@@ -230,3 +254,17 @@ class Transport:
 
     def probe(self, what, idx, x):
         return sput_probe(self.h, what, idx, x)
+
+    def autotune(self, sample_tickets=20_000_000, stream=None, **kw):
+        """Time candidate launch shapes on a sample and keep the fastest as this scene's default."""
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        return sput_autotune(self.h, run_opts(seed=self.scene.seed, **kw), s, self._tal, sample_tickets)
+
+    def graph(self, stream=None, **kw):
+        """CUDA graph of one run into this object's tallies; replay with graph_launch(g, seed)."""
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        return sput_graph_create(self.h, run_opts(seed=self.scene.seed, **kw), s, self._tal)

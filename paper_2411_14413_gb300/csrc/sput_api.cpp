@@ -114,6 +114,9 @@ struct sput_scene {
     size_t stage_bytes = 0;
     cudaStream_t own_stream = nullptr;
     Params base{};
+    int smem_counters_fit = 0;  // per-primitive counters fit in shared memory
+    // launch shape for opts fields left 0 (set by sput_autotune)
+    int def_threads = 256, def_bps = 0, def_chunk = 32, def_flags = 0;
 };
 
 namespace {
@@ -545,6 +548,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
             return fail(SPUT_ERR_UNSUPPORTED, "scene tables exceed the shared memory of one block");
         }
     }
+    S->smem_counters_fit = p.smem_counters;
     *out = S;
     return SPUT_OK;
 }
@@ -628,10 +632,13 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     if (T->hist_A && S->grid.n_abins == 0) return fail(SPUT_ERR_INVALID_ARG, "hist_A requested but n_abins = 0");
     unsigned long long tb = opts->ticket_begin, te = opts->ticket_end ? opts->ticket_end : S->n_tickets;
     if (tb > te || te > S->n_tickets) return fail(SPUT_ERR_INVALID_ARG, "ticket range outside [0, n_tickets]");
-    int threads = opts->block_threads ? opts->block_threads : 256;
+    int threads = opts->block_threads ? opts->block_threads : S->def_threads;
     if (threads < 32 || threads > 256 || threads % 32) return fail(SPUT_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
-    int chunk = opts->ticket_chunk ? opts->ticket_chunk : 32;
+    int chunk = opts->ticket_chunk ? opts->ticket_chunk : S->def_chunk;
     if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
+    const int flags = opts->flags ? opts->flags : S->def_flags;
+    if (flags & ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS)) return fail(SPUT_ERR_INVALID_ARG, "unknown flags");
+    const int bps_req = opts->blocks_per_sm ? opts->blocks_per_sm : S->def_bps;
 
     Params p = S->base;
     p.counts = T->counts;
@@ -650,6 +657,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     p.ticket_counter = scratch;
     p.stats = scratch + 1;
     p.status = reinterpret_cast<unsigned int*>(scratch + 1 + kNumStats);
+    p.smem_counters = (flags & SPUT_RUN_NO_SMEM_COUNTERS) ? 0 : S->smem_counters_fit;
 
     const TallySizes sz = tally_sizes(S);
     if (!opts->accumulate) {
@@ -667,7 +675,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     const size_t smem = transport_smem_bytes(p);
     int bps = transport_max_blocks_per_sm(c64, threads, smem);
     if (bps < 1) return fail(SPUT_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
-    if (opts->blocks_per_sm > 0) bps = std::min(bps, opts->blocks_per_sm);
+    if (bps_req > 0) bps = std::min(bps, bps_req);
     unsigned long long need = (te - tb + threads - 1) / threads;
     int blocks = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>((unsigned long long)S->n_sm * bps, need));
     if (te == tb) blocks = 1;
@@ -819,12 +827,194 @@ sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* str
     stats->attempts = h[6];
     stats->device_status = (uint32_t)(h[1 + kNumStats] & 0xffffffffu);
     stats->grid_blocks = 0;
-    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : 256);
+    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : S->def_threads);
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, S->ev0, S->ev1);
     stats->kernel_ms = ms;
     if (stats->device_status) return fail(SPUT_ERR_DEVICE_CHECK, "device status bits set");
     return SPUT_OK;
+}
+
+sput_status sput_autotune(sput_scene* S, const sput_run_opts* base, void* stream, const sput_tallies* T,
+                          uint64_t sample_tickets, sput_tune_result* out)
+{
+    if (!S || !base || !T || !out) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(S->device);
+    sput_status st = ensure_scratch(S);
+    if (st != SPUT_OK) return st;
+    std::memset(out, 0, sizeof *out);
+    const unsigned long long n = S->n_tickets;
+    if (n == 0) return fail(SPUT_ERR_INVALID_ARG, "scene has no particles");
+    // four equal ticket ranges spread over the ticket space
+    const unsigned long long per = std::max<unsigned long long>(1ull, std::min<unsigned long long>(sample_tickets / 4, n / 4 ? n / 4 : n));
+    unsigned long long rb[4], re[4];
+    int nr = 0;
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long b = (n / 4) * i;
+        if (b >= n) break;
+        rb[nr] = b;
+        re[nr] = std::min(n, b + per);
+        ++nr;
+    }
+    struct Cand { int threads, bps, chunk, flags; };
+    std::vector<Cand> cands;
+    const int c64 = S->grid.count_type == SPUT_COUNT_INT64;
+    for (int threads : {128, 192, 256}) {
+        Params probe = S->base;
+        probe.smem_counters = S->smem_counters_fit;
+        const int occ = transport_max_blocks_per_sm(c64, threads, transport_smem_bytes(probe));
+        for (int fl : {SPUT_RUN_SMEM_COUNTERS, SPUT_RUN_NO_SMEM_COUNTERS}) {
+            if (fl == SPUT_RUN_SMEM_COUNTERS && !S->smem_counters_fit) continue;
+            Params pr = S->base;
+            pr.smem_counters = fl == SPUT_RUN_SMEM_COUNTERS ? 1 : 0;
+            const int maxb = transport_max_blocks_per_sm(c64, threads, transport_smem_bytes(pr));
+            if (maxb < 1) continue;
+            for (int bps : {maxb, maxb - 1})
+                if (bps >= 1 && (bps == maxb || bps >= occ - 1))
+                    for (int chunk : {32, 128}) cands.push_back(Cand{threads, bps, chunk, fl});
+        }
+    }
+    if (cands.size() > 32) cands.resize(32);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double best = -1.0;
+    Cand bestc = cands.empty() ? Cand{256, 0, 32, 0} : cands[0];
+    for (size_t ci = 0; ci <= cands.size(); ++ci) {
+        // candidate 0 is timed twice: the first pass warms up
+        const Cand c = cands[ci == 0 ? 0 : ci - 1];
+        double coll = 0.0, ms = 0.0;
+        for (int r = 0; r < nr; ++r) {
+            sput_run_opts o = *base;
+            o.ticket_begin = rb[r];
+            o.ticket_end = re[r];
+            o.block_threads = c.threads;
+            o.blocks_per_sm = c.bps;
+            o.ticket_chunk = c.chunk;
+            o.flags = c.flags;
+            o.accumulate = 0;
+            sput_run_stats rs{};
+            st = run_impl(S, &o, s, T, &rs, S->d_scratch);
+            if (st != SPUT_OK) return st;
+            coll += (double)rs.collisions;
+            ms += rs.kernel_ms;
+        }
+        if (ci == 0) continue;
+        const double rate = ms > 0.0 ? coll / (ms * 1e-3) : 0.0;
+        const int k = out->n_candidates++;
+        out->cand_threads[k] = c.threads;
+        out->cand_bps[k] = c.bps;
+        out->cand_chunk[k] = c.chunk;
+        out->cand_flags[k] = c.flags;
+        out->cand_rate[k] = (float)rate;
+        if (rate > best) {
+            best = rate;
+            bestc = c;
+        }
+    }
+    S->def_threads = bestc.threads;
+    S->def_bps = bestc.bps;
+    S->def_chunk = bestc.chunk;
+    S->def_flags = bestc.flags;
+    out->block_threads = bestc.threads;
+    out->blocks_per_sm = bestc.bps;
+    out->ticket_chunk = bestc.chunk;
+    out->flags = bestc.flags;
+    out->best_rate = (float)best;
+    return SPUT_OK;
+}
+
+}  // extern "C"
+
+struct sput_graph {
+    sput_scene* S = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+    cudaKernelNodeParams kp{};
+    Params params{};
+    void* args[1] = {nullptr};
+    cudaStream_t cs = nullptr;
+};
+
+extern "C" {
+
+sput_status sput_graph_create(sput_scene* S, const sput_run_opts* opts, void* stream, const sput_tallies* T,
+                              sput_graph** out)
+{
+    if (!S || !opts || !T || !out) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    DeviceGuard guard(S->device);
+    sput_status st = ensure_scratch(S);
+    if (st != SPUT_OK) return st;
+    sput_graph* G = new sput_graph();
+    G->S = S;
+    (void)stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(G->cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        sput_graph_destroy(G);
+        return cuda_fail(e, "graph capture begin");
+    }
+    st = run_impl(S, opts, G->cs, T, nullptr, S->d_scratch);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(G->cs, &g);
+    G->graph = g;
+    if (st != SPUT_OK) {
+        sput_graph_destroy(G);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        sput_graph_destroy(G);
+        return cuda_fail(e, "graph capture end");
+    }
+    size_t nn = 0;
+    e = cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+        cudaGraphNodeType ty;
+        e = cudaGraphNodeGetType(nodes[i], &ty);
+        if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel) G->knode = nodes[i];
+    }
+    if (e == cudaSuccess && G->knode) e = cudaGraphKernelNodeGetParams(G->knode, &G->kp);
+    if (e != cudaSuccess || !G->knode) {
+        sput_graph_destroy(G);
+        return e != cudaSuccess ? cuda_fail(e, "graph inspection") : fail(SPUT_ERR_CUDA, "no kernel node in the captured graph");
+    }
+    std::memcpy(&G->params, G->kp.kernelParams[0], sizeof(Params));
+    e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess) {
+        sput_graph_destroy(G);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    *out = G;
+    return SPUT_OK;
+}
+
+sput_status sput_graph_launch(sput_graph* G, uint64_t seed, void* stream)
+{
+    if (!G) return fail(SPUT_ERR_INVALID_ARG, "graph is NULL");
+    DeviceGuard guard(G->S->device);
+    G->params.key0 = (uint32_t)seed;
+    G->params.key1 = (uint32_t)(seed >> 32);
+    G->args[0] = &G->params;
+    cudaKernelNodeParams kp = G->kp;
+    kp.kernelParams = G->args;
+    kp.extra = nullptr;
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(G->exec, G->knode, &kp));
+    CUDA_TRY(cudaGraphLaunch(G->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return SPUT_OK;
+}
+
+void sput_graph_destroy(sput_graph* G)
+{
+    if (!G) return;
+    {
+        DeviceGuard guard(G->S ? G->S->device : 0);
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        if (G->graph) cudaGraphDestroy(G->graph);
+        if (G->cs) cudaStreamDestroy(G->cs);
+    }
+    delete G;
 }
 
 void sput_scene_destroy(sput_scene* S)

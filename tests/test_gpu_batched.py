@@ -1,0 +1,111 @@
+"""Batched instances (cathodes x process conditions, uneven particle counts) in
+one launch, the autotuner and CUDA-graph replay -- all through the C ABI.
+
+The batched launch replaces the paper's split of an n-cathode system into n
+single-cathode runs (Sec. "The SIMTRA Python wrapper"): every instance keeps
+its own random streams, so one launch over all instances gives exactly the
+tallies of one launch per instance."""
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2411_14413_gb300 as p
+    p.build()
+    return p
+
+
+def _small_sweep():
+    # the 4 cathodes x 16 pressures x 8 tilts sweep with small uneven counts
+    return workloads.scene_tilt_pressure_sweep(n_range=(20, 300))
+
+
+def test_sweep_batched_equals_per_instance(torch, pkg):
+    sc = _small_sweep()
+    assert len(sc.instances) == 512 and len(sc.geometries) == 8
+    tr = pkg.Transport(sc)
+    st = tr.run(seed=3)
+    assert st.particles == sc.total_particles
+    batched = {k: v.clone() for k, v in tr.t.items()}
+    # one launch per instance over its own ticket range, accumulated
+    off = 0
+    for i, inst in enumerate(sc.instances):
+        tr.run(seed=3, ticket_begin=off, ticket_end=off + inst["n"], accumulate=i > 0, want_stats=False)
+        off += inst["n"]
+    torch.cuda.synchronize()
+    for k in batched:
+        assert torch.equal(batched[k], tr.t[k]), k
+    assert int(tr.t["prim_counts"].sum() + tr.t["timed_out"].sum()) == sc.total_particles
+    tr.close()
+
+
+def test_sweep_sampled_parity_with_oracle(torch, pkg, oracle_mod):
+    """Per-particle landing parity across all 8 tilted geometries and 16 pressures."""
+    sc = _small_sweep()
+    tr = pkg.Transport(sc, records=True)
+    tr.run()
+    rec = tr.records()
+    tr.close()
+    prefix = np.concatenate([[0], np.cumsum([i["n"] for i in sc.instances])])
+    rng = np.random.default_rng(9)
+    tick = np.sort(rng.choice(prefix[-1], 3000, replace=False))
+    inst = np.searchsorted(prefix, tick, side="right") - 1
+    pid = tick - prefix[inst]
+    o = oracle_mod.OracleScene(sc).run_ids(inst.astype(np.int32), pid.astype(np.uint64))
+    same = (rec["prim"][tick] == o["prim"]) & (rec["cell"][tick] == o["cell"])
+    n = len(same)
+    allowed = 0.001 * n + 3 * np.sqrt(0.001 * n) + 1
+    assert (~same).sum() <= allowed, ((~same).sum(), allowed)
+
+
+def test_autotune_sets_scene_default(torch, pkg):
+    sc = workloads.scene_quaternary(n_per_cathode=100_000)
+    tr = pkg.Transport(sc)
+    res = tr.autotune(sample_tickets=200_000)
+    cands = res.candidates()
+    assert res.n_candidates >= 4 and all(c["rate"] > 0 for c in cands)
+    assert res.best_rate == max(c["rate"] for c in cands)
+    st = tr.run(seed=7)
+    assert st.block_threads == res.block_threads
+    ref = {k: v.clone() for k, v in tr.t.items()}
+    tr.run(seed=7, block_threads=64, blocks_per_sm=1, ticket_chunk=3, flags=1)
+    for k in ref:
+        assert torch.equal(ref[k], tr.t[k]), k
+    tr.close()
+
+
+def test_graph_replay_matches_runs(torch, pkg):
+    from paper_2411_14413_gb300 import api
+
+    sc = workloads.scene_quaternary(n_per_cathode=50_000)
+    tr = pkg.Transport(sc, energy=True)
+    want = {}
+    for seed in (3, 4):
+        tr.run(seed=seed)
+        want[seed] = {k: v.clone() for k, v in tr.t.items()}
+    g = tr.graph()
+    stream = torch.cuda.current_stream().cuda_stream
+    try:
+        for seed in (4, 3, 4):
+            api.sput_graph_launch(g, seed, stream)
+            torch.cuda.synchronize()
+            for k in ("counts", "prim_counts", "timed_out"):
+                assert torch.equal(want[seed][k], tr.t[k]), (seed, k)
+            rel = (tr.t["energy"] - want[seed]["energy"]).abs().max() / want[seed]["energy"].abs().max()
+            assert float(rel) < 1e-12
+    finally:
+        api.sput_graph_destroy(g)
+        tr.close()
