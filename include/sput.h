@@ -332,6 +332,45 @@ sput_status sput_graph_create(sput_scene* scene, const sput_run_opts* opts, void
 sput_status sput_graph_launch(sput_graph* graph, uint64_t seed, void* stream);
 void sput_graph_destroy(sput_graph* graph);
 
+/* Likelihood-ratio backward pass for the gas pressure.  Pressure enters only
+ * through the free flights (Eq. for lambda with lambda_m = v/(n_g <sigma g>),
+ * n_g = p/(k_B T)); the forward run accumulates, per tally cell, the score
+ * S = sum over collisions (1 - l_k/lambda_k) - t_land/lambda_land = d ln p(path)/d ln n_g
+ * of every landing atom (sput_tallies.score).  Then d E[count]/d ln p equals the
+ * expected score tally, and for a loss L
+ *   grad_log_pressure[i] = sum_cells grad_counts[i][cell] * score_tally[i][cell]
+ * estimates dL/d ln p_i.  All pointers are DEVICE arrays in the tally layout of
+ * `scene` ([n_instances][ny][nx], double; output [n_instances]).  Asynchronous on
+ * `stream`.  The paper computes no gradients; this is the adjoint of its transport. */
+sput_status sput_backward(const sput_scene* scene, const double* grad_counts, const double* score_tally,
+                          double* grad_log_pressure, void* stream);
+
+/* Arrival counts -> composition in at.% (Methods paragraph after Table 1: arrival
+ * fractions weighted with the sputter rates, then with bulk density and atomic
+ * mass).  For cathode j and measurement point m,
+ *   a_j(m) = R_j(P_j) N_j(m)/N_j(ref) rho_j/M_j,   composition[m][j] = 100 a_j(m) / sum_k a_k(m),
+ * N_j(m) the counts of cathode j summed over the cells with patch_of_cell == m, ref
+ * the reference point, R_j(P) the line through the two calibration points.
+ *   counts         DEVICE int64 [n_cathodes][n_cells] (the first n_cathodes instances' counts)
+ *   patch_of_cell  DEVICE int32 [n_cells], point index or -1
+ *   calibration    HOST double [n_cathodes][6] = (P_a, R_a, P_b, R_b, density, atomic mass)
+ *   power          HOST double [n_cathodes]
+ *   patch_counts   DEVICE double [n_cathodes][n_points] (output, kept for the backward pass)
+ *   composition    DEVICE double [n_points][n_cathodes] (output)
+ * n_cathodes <= 16.  Asynchronous on `stream`. */
+sput_status sput_composition(int n_cathodes, int n_cells, int n_points, const int64_t* counts,
+                             const int32_t* patch_of_cell, int ref_point, const double* calibration,
+                             const double* power, double* patch_counts, double* composition, void* stream);
+
+/* Backward pass of sput_composition: from grad_composition (DEVICE [n_points][n_cathodes])
+ * and the forward's patch_counts, writes grad_patch (DEVICE [n_cathodes][n_points], scratch
+ * owned by the caller), grad_counts (DEVICE double [n_cathodes][n_cells]) and grad_power
+ * (DEVICE double [n_cathodes], through dR_j/dP_j).  Asynchronous on `stream`. */
+sput_status sput_composition_backward(int n_cathodes, int n_cells, int n_points, const double* patch_counts,
+                                      const int32_t* patch_of_cell, int ref_point, const double* calibration,
+                                      const double* power, const double* grad_composition, double* grad_patch,
+                                      double* grad_counts, double* grad_power, void* stream);
+
 /* Free the scene and its device memory. */
 void sput_scene_destroy(sput_scene* scene);
 

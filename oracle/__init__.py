@@ -372,3 +372,40 @@ def tally(scene, out):
         res["hist_A"] = np.bincount(inst[on_grid] * g["n_abins"] + ab,
                                     minlength=n_inst * g["n_abins"]).reshape(n_inst, -1)
     return res
+
+
+# ---------------------------------------------------------------- composition
+def rate_line(points, power):
+    """Sputter rate at `power` on the line through two (power, rate) points
+    (linear power-rate relation of Fig. 4a / Table S1); returns (rate, slope)."""
+    (p1, r1), (p2, r2) = points
+    slope = (r2 - r1) / (p2 - p1)
+    return r1 + slope * (power - p1), slope
+
+
+def composition(counts, patch_of_cell, ref, rates, density, mass):
+    """Arrival counts -> at.% (Methods paragraph after Table 1): the arrival
+    fraction of element j at point m relative to the reference point, weighted
+    with the sputter rate, then with bulk density / atomic mass, normalised.
+    counts: [n_cath][n_cells]; returns comp [n_points][n_cath] and N [n_cath][n_points]."""
+    counts = np.asarray(counts, dtype=np.float64)
+    n_points = int(np.max(patch_of_cell)) + 1
+    n_cath = counts.shape[0]
+    N = np.zeros((n_cath, n_points))
+    for j in range(n_cath):
+        sel = patch_of_cell >= 0
+        N[j] = np.bincount(patch_of_cell[sel], weights=counts[j][sel], minlength=n_points)
+    a = np.empty((n_points, n_cath))
+    for j in range(n_cath):
+        a[:, j] = rates[j] * N[j] / N[j, ref] * density[j] / mass[j]
+    return 100.0 * a / a.sum(axis=1, keepdims=True), N
+
+
+def lr_gradient(outcomes, n_inst, n_cells, grad_counts):
+    """Likelihood-ratio estimate of dL/d ln p per instance from per-particle
+    scores: sum over landing particles of dL/dcount[cell] * score."""
+    g = np.zeros(n_inst)
+    on = outcomes["cell"] >= 0
+    gc = np.asarray(grad_counts).reshape(n_inst, n_cells)
+    np.add.at(g, outcomes["inst"][on], gc[outcomes["inst"][on], outcomes["cell"][on]] * outcomes["score"][on])
+    return g

@@ -20,7 +20,7 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libsput.so")
-SOURCES = ["sput_api.cpp", "sput_tables.cpp", "sput_transport.cu"]
+SOURCES = ["sput_api.cpp", "sput_tables.cpp", "sput_transport.cu", "sput_adjoint.cu"]
 HEADERS = ["sput_internal.h", "sput_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -201,6 +201,10 @@ SIGNATURES = {
     "sput_graph_create": (C.c_int, [_P, C.POINTER(sput_run_opts), _P, C.POINTER(sput_tallies), C.POINTER(_P)]),
     "sput_graph_launch": (C.c_int, [_P, C.c_uint64, _P]),
     "sput_graph_destroy": (None, [_P]),
+    "sput_backward": (C.c_int, [_P, _P, _P, _P, _P]),
+    "sput_composition": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P]),
+    "sput_composition_backward": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
+                                            _P]),
     "sput_probe": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
 }
 

@@ -74,6 +74,8 @@ double thompson_emax(double k, double Mi, double Mt, double Ei, double Us)
 
 }  // namespace
 
+void sput::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct sput_scene {
     int device = 0;
     int n_sm = 0;

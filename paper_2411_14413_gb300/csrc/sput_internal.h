@@ -151,6 +151,9 @@ size_t transport_smem_bytes(const Params& p);
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem);
 int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev, double* y_dev, void* stream);
 
+// Error text for sput_last_error from other translation units.
+void set_last_error(const char* msg);
+
 // Static run scratch of sput_run_noalloc (module memory, no allocation).
 constexpr size_t kRunScratchBytes = 64;      // ticket counter + kNumStats statistics + status word
 constexpr size_t kStaticScratchBytes = 256;  // capacity of the static array

@@ -1,0 +1,200 @@
+"""Likelihood-ratio gradients and the composition map (GPU, through the C ABI).
+
+The score accumulated per landing atom is d ln p(path)/d ln n_g: flights
+that end in a collision contribute 1 - l/lambda, the final flight -t/lambda
+(Eq. for lambda).  Checks: per-particle scores against the oracle's, zero
+mean, the closed-form derivative of the survival fraction 2 E_3(kappa)
+(constant lambda), common-random-number finite differences, and the
+composition map's forward/backward against numpy and finite differences."""
+
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+import workloads
+from workloads import ELEMENTS
+from workloads.measurement import calibration_points, measurement_patches
+
+pytestmark = pytest.mark.gpu
+
+QUAT = ("Ni", "Pd", "Pt", "Ru")
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2411_14413_gb300 as p
+    p.build()
+    return p
+
+
+def _calibration():
+    cal = []
+    for s in QUAT:
+        (p1, r1), (p2, r2) = calibration_points(s)
+        cal.append([p1, r1, p2, r2, ELEMENTS[s].density, ELEMENTS[s].mass])
+    return np.array(cal)
+
+
+def test_score_matches_oracle_and_has_zero_mean(torch, pkg, oracle_mod):
+    sc = workloads.scene_quaternary(n_per_cathode=2000)
+    tr = pkg.Transport(sc, records=True, score=True)
+    tr.run()
+    g = tr.records()
+    score_tally = tr.t["score"].cpu().numpy()
+    tr.close()
+    o = oracle_mod.OracleScene(sc).run_all()
+    same = (g["prim"] == o["prim"]) & (g["ncoll"] == o["ncoll"])
+    assert same.mean() > 0.99
+    err = np.abs(g["score"][same] - o["score"][same])
+    assert np.max(err / (1 + np.abs(o["score"][same]))) < 1e-3, np.max(err)
+    # the score tally is the sum of the landing particles' scores per cell
+    inst = np.repeat(np.arange(4), 2000)
+    on = g["cell"] >= 0
+    want = np.zeros(score_tally.size)
+    np.add.at(want, inst[on] * 40000 + g["cell"][on], g["score"][on])
+    assert np.allclose(score_tally.ravel(), want, rtol=1e-9, atol=1e-9)
+    # E[S] = 0 (the path density integrates to one for every pressure)
+    big = workloads.scene_quaternary(n_per_cathode=100_000)
+    tr = pkg.Transport(big, records=True)
+    tr.run(seed=5)
+    s = tr.records()["score"]
+    tr.close()
+    assert abs(s.mean()) < 4 * s.std() / math.sqrt(len(s))
+
+
+def test_lr_derivative_of_survival_closed_form(torch, pkg):
+    """Constant lambda (hard spheres, gas at rest): P(reach a plane at height L
+    without collision) = 2 E_3(kappa), kappa = n sigma L, so
+    dP/d ln p = -2 kappa E_2(kappa).  The LR estimate is mean(1{no collision} S)."""
+    from workloads.scenes import _prim, default_grid, default_physics
+
+    d_hs, L = 3.0, 40.0
+    sigma = math.pi * d_hs**2 * 1e-14
+    p = (1.0 / (sigma * L)) * 1e9 * 1.380649e-23 * 300.0
+    big = 1e7
+    prims = [_prim("box"), _prim("disc", (0, 0, 0), (1, 0, 0), (0, 1, 0), 0.0, 25.4),
+             _prim("rect", (0, 0, L), (1, 0, 0), (0, -1, 0), big, big)]
+    cath = [{"element": ELEMENTS["Ni"], "center": (0, 0, 0), "normal": (0, 0, 1), "e1": (1, 0, 0),
+             "racetrack": {"kind": "gaussian_annulus", "r0": 12.0, "sigma": 3.0, "R": 25.4},
+             "cos_coef": (0, 1, 0, 0, 0, 0), "target": 1}]
+    n = 4_000_000
+    sc = workloads.Scene("open", (-big, -big, -big), (big, big, big), workloads.GAS_AR, 300.0, prims,
+                         [{"prim_begin": 0, "prim_count": 3, "substrate": 2}], cath,
+                         [{"geometry": 0, "cathode": 0, "pressure": p, "E_i": 400.0, "k": 0.4, "n": n}],
+                         default_grid(4, 4, 50.0, 50.0),
+                         default_physics(interaction="hard_sphere", hs_diameter=d_hs, gas_motion="stationary",
+                                         max_collisions=100), 0)
+    tr = pkg.Transport(sc, records=True)
+    tr.run()
+    r = tr.records()
+    tr.close()
+    kappa = 1.0 * (p / ((1.0 / (sigma * L)) * 1e9 * 1.380649e-23 * 300.0))
+    f = ((r["prim"] == 2) & (r["ncoll"] == 0)).astype(float)
+    est = f * r["score"]
+    want = -2 * kappa * special.expn(2, kappa)
+    assert abs(est.mean() - want) < 4 * est.std() / math.sqrt(n), (est.mean(), want)
+    assert abs(f.mean() - 2 * special.expn(3, kappa)) < 4 * f.std() / math.sqrt(n)
+
+
+def test_lr_gradient_matches_crn_finite_difference(torch, pkg):
+    """d/d ln p of the substrate arrivals in a central region: LR against
+    central finite differences with common random numbers (same seed)."""
+    from paper_2411_14413_gb300 import _native as N
+
+    sc = workloads.scene_quaternary(n_per_cathode=1_000_000)
+    tr = pkg.Transport(sc, score=True)
+    nx = sc.grid["nx"]
+    w = torch.zeros((4, 200, 200), dtype=torch.float64, device="cuda")
+    w[:, 60:140, 60:140] = 1.0
+    grad = torch.zeros(4, dtype=torch.float64, device="cuda")
+    lr, fd = [], []
+    h = 0.05
+    for seed in range(4):
+        tr.set_instances(sc)
+        tr.run(seed=seed)
+        N.check(N.load().sput_backward(tr.h, w.data_ptr(), tr.t["score"].data_ptr(), grad.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream), "sput_backward")
+        torch.cuda.synchronize()
+        lr.append(grad.cpu().numpy().copy())
+        vals = []
+        for s in (+1, -1):
+            tr.set_instances(sc.with_pressure(0.5 * math.exp(s * h)))
+            tr.run(seed=seed)
+            vals.append((tr.t["counts"].double() * w).sum(dim=(1, 2)).cpu().numpy())
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    tr.close()
+    lr, fd = np.array(lr), np.array(fd)
+    for j in range(4):
+        se = math.sqrt(lr[:, j].var(ddof=1) / 4 + fd[:, j].var(ddof=1) / 4)
+        assert abs(lr[:, j].mean() - fd[:, j].mean()) < 5 * se + 0.02 * abs(fd[:, j].mean()), (j, lr[:, j], fd[:, j])
+
+
+def test_composition_kernels_against_numpy_and_fd(torch, pkg, oracle_mod):
+    from paper_2411_14413_gb300.adjoint import MapSetup
+
+    patch, pts, ref = measurement_patches()
+    sc = workloads.scene_quaternary(n_per_cathode=400_000)
+    cal = _calibration()
+    ms = MapSetup(sc, patch, ref, cal)
+    power = np.array([20.0, 30.0, 12.0, 18.0])
+    comp = ms.forward(0.5, power, seed=1).cpu().numpy()
+    counts = ms.tr.t["counts"].cpu().numpy().reshape(4, -1).astype(np.float64)
+    rates = np.array([oracle_mod.rate_line(calibration_points(s), P)[0] for s, P in zip(QUAT, power)])
+    want, _ = oracle_mod.composition(counts, patch, ref, rates, cal[:, 4], cal[:, 5])
+    assert np.allclose(comp, want, rtol=1e-12, atol=1e-10)
+    # backward: dL/dP against central differences of the deterministic map (same counts)
+    rng = np.random.default_rng(3)
+    gcomp = torch.as_tensor(rng.normal(size=comp.shape), device="cuda")
+    _, gpow = ms.backward(gcomp, power)
+    gpow = gpow.cpu().numpy()
+    for j in range(4):
+        e = np.zeros(4)
+        e[j] = 1e-4
+        rp = np.array([oracle_mod.rate_line(calibration_points(s), P)[0] for s, P in zip(QUAT, power + e)])
+        rm = np.array([oracle_mod.rate_line(calibration_points(s), P)[0] for s, P in zip(QUAT, power - e)])
+        cp, _ = oracle_mod.composition(counts, patch, ref, rp, cal[:, 4], cal[:, 5])
+        cm, _ = oracle_mod.composition(counts, patch, ref, rm, cal[:, 4], cal[:, 5])
+        fdj = float((gcomp.cpu().numpy() * (cp - cm)).sum() / 2e-4)
+        assert abs(gpow[j] - fdj) < 1e-5 * (1 + abs(fdj)), (j, gpow[j], fdj)
+    # dL/dcounts against finite differences of one patch's counts
+    gcounts = ms.grad_counts.cpu().numpy()
+    for j, m in [(0, 5), (2, ref), (3, 200)]:
+        cells = np.nonzero(patch == m)[0]
+        cp_, cm_ = counts.copy(), counts.copy()
+        cp_[j, cells[0]] += 1e-3
+        cm_[j, cells[0]] -= 1e-3
+        fp, _ = oracle_mod.composition(cp_, patch, ref, rates, cal[:, 4], cal[:, 5])
+        fm, _ = oracle_mod.composition(cm_, patch, ref, rates, cal[:, 4], cal[:, 5])
+        fdj = float((gcomp.cpu().numpy() * (fp - fm)).sum() / 2e-3)
+        assert abs(gcounts[j, cells[0]] - fdj) < 1e-6 * (1 + abs(fdj)), (j, m, gcounts[j, cells[0]], fdj)
+    ms.close()
+
+
+def test_inverse_solve_reduces_error(torch, pkg):
+    """50 Adam steps with common random numbers from a wrong start: the composition
+    error drops by more than 10x and the power ratios move towards the truth."""
+    from paper_2411_14413_gb300.adjoint import MapSetup, inverse_solve
+
+    patch, pts, ref = measurement_patches()
+    sc = workloads.scene_quaternary(n_per_cathode=500_000)
+    ms = MapSetup(sc, patch, ref, _calibration())
+    true_p, true_pw = 0.7, np.array([25.0, 40.0, 10.0, 20.0])
+    target = ms.forward(true_p, true_pw, seed=0).clone()
+    start = np.array([12.0, 20.0, 20.0, 10.0])
+    hist = inverse_solve(ms, target, math.log(0.4), start, steps=50, lr=0.1, seed=0)
+    ms.close()
+    best = min(h["loss"] for h in hist[-10:])
+    assert best < 0.1 * hist[0]["loss"], (hist[0]["loss"], best)
+    frac = lambda x: np.asarray(x) / np.sum(x)
+    err0 = np.abs(frac(start) - frac(true_pw)).max()
+    err1 = np.abs(frac(hist[-1]["power"]) - frac(true_pw)).max()
+    assert err1 < 0.5 * err0, (err0, err1, hist[-1]["power"])
