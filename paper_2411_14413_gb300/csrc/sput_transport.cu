@@ -26,8 +26,10 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ----------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
-// multiplies with the published multipliers and Weyl key increments.
-__device__ __forceinline__ uint4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+// multiplies with the published multipliers and Weyl key increments.  Kept
+// out of line: one copy instead of one per call site keeps the hot loop small
+// enough for the instruction cache.
+__device__ __noinline__ uint4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
                                         uint32_t c3)
 {
 #pragma unroll
@@ -128,7 +130,8 @@ __device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
     // for x > 23 (d = 1.2) and x > 4 (d = 6.0).  Both x-bounds hold from the start
     // of the apsis iteration onwards because x only grows from max(beta, x_h).
     const bool t1 = x < 23.0f, t2 = x < 4.0f;
-#pragma unroll
+    // loops are not unrolled: a compact kernel misses the instruction cache less
+#pragma unroll 1
     for (int it = 0; it < kApsisIters; ++it) {
         float e0 = kMolC0 * expf(-kMolD0 * x);
         float e1 = t1 ? kMolC1 * expf(-kMolD1 * x) : 0.0f;
@@ -151,7 +154,7 @@ __device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
     const float p2 = u2 ? kMolC2 * expf(-kMolD2 * x0) * iex : 0.0f;
     const float y0 = kMolD0 * x0, y1 = kMolD1 * x0, y2 = kMolD2 * x0;
     float s = 0.0f;
-#pragma unroll 4
+#pragma unroll 1
     for (int j = 0; j < kGMHalf; ++j) {
         const float4 nd = gm[j];  // (u, 1/(1+u), u/(1-u^2), 1/u - 1)
         float D = p0 * fmaf(nd.z, one_minus_exp_neg(y0 * nd.w), nd.y);
