@@ -33,10 +33,12 @@
  * word, seed high word) and counter = (particle id, instance, event, block).
  * Event 0 is the launch (block 0: racetrack radius, racetrack azimuth, energy,
  * polar cosine; block 1 word 0: emission azimuth).  Event k >= 1 is flight k
- * (block 0: flight length, impact parameter, scattering azimuth, acceptance
- * of partner attempt 0; block 1+a: the three Maxwellian components of attempt
- * a by Box-Muller; block 1+A+(a-1)/4 word (a-1)%4: acceptance of attempt a>=1,
- * A = max_attempts).  A 32-bit word x maps to RN = ((x >> 8) + 1) * 2^-24.
+ * (block 0: flight length, impact parameter, scattering azimuth; block 1+a,
+ * a < max_attempts: partner attempt a, the three Maxwellian components by
+ * Box-Muller from its four words, and its acceptance uniform from the low
+ * bytes of words 0, 1, 2 joined as x = (w0 & 255) << 24 | (w1 & 255) << 16 |
+ * (w2 & 255) << 8).  A 32-bit word x maps to RN = ((x >> 8) + 1) * 2^-24,
+ * which uses only its upper 24 bits.
  * Every particle therefore has its own stream: integer tallies are bit-exact
  * and independent of launch configuration, order and chunking.
  *

@@ -702,9 +702,12 @@ static void collide_with(const or_scene* S, const cath_t* c, const double v[3], 
     if (chi_out) *chi_out = chi;
 }
 
-/* gas partner: Maxwellian weighted by sigma(g) g, by rejection */
-static int sample_partner(const or_scene* S, const cath_t* c, const stream_t* st, uint32_t event, double u_acc0,
-                          const double v[3], double V[3])
+/* gas partner: Maxwellian weighted by sigma(g) g, by rejection.  Attempt a
+ * draws Philox block 1 + a of the flight's event: the upper 24 bits of its four
+ * words give the Box-Muller pairs (three components used), and the low bytes of
+ * words 0, 1, 2, joined into one more 24-bit number, the acceptance uniform. */
+static int sample_partner(const or_scene* S, const cath_t* c, const stream_t* st, uint32_t event, const double v[3],
+                          double V[3])
 {
     if (S->gas_motion == GAS_STATIONARY) {
         V[0] = V[1] = V[2] = 0.0;
@@ -714,19 +717,15 @@ static int sample_partner(const or_scene* S, const cath_t* c, const stream_t* st
     double Mv = M_of_v(S, c, speed);
     double s = S->s_gas;
     int A = S->max_attempts;
-    uint32_t w[4], wa[4];
+    uint32_t w[4];
     for (int a = 0; a < A; ++a) {
         draw(st, event, 1u + (uint32_t)a, w);
         double R0 = sqrt(-2.0 * log(rn(w[0]))), R1 = sqrt(-2.0 * log(rn(w[2])));
         V[0] = s * R0 * cos(2.0 * M_PI * rn(w[1]));
         V[1] = s * R0 * sin(2.0 * M_PI * rn(w[1]));
         V[2] = s * R1 * cos(2.0 * M_PI * rn(w[3]));
-        double ua;
-        if (a == 0) ua = u_acc0;
-        else {
-            draw(st, event, 1u + (uint32_t)A + (uint32_t)((a - 1) / 4), wa);
-            ua = rn(wa[(a - 1) % 4]);
-        }
+        uint32_t low = ((w[0] & 0xffu) << 24) | ((w[1] & 0xffu) << 16) | ((w[2] & 0xffu) << 8);
+        double ua = rn(low);
         double gv[3] = {v[0] - V[0], v[1] - V[1], v[2] - V[2]};
         double g = sqrt(dot3(gv, gv));
         if (ua * Mv <= h_of_g(S, c, g)) return a + 1;
@@ -840,7 +839,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         }
         for (int a = 0; a < 3; ++a) v[a] = speed * d[a];
         double V[3], vo[3], Vo[3];
-        int na = sample_partner(S, c, &st, k, rn(w[3]), v, V);
+        int na = sample_partner(S, c, &st, k, v, V);
         attempts += na;
         collide_with(S, c, v, V, rn(w[1]), rn(w[2]), vo, Vo, NULL);
         speed = sqrt(dot3(vo, vo));
@@ -1061,9 +1060,7 @@ void or_collide(const or_scene* S, int c, const double* v, const double* V, doub
 int or_partner(const or_scene* S, uint64_t seed, int inst, uint64_t pid, uint32_t event, const double* v, double* V)
 {
     stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, (uint32_t)inst};
-    uint32_t w[4];
-    draw(&st, event, 0u, w);
-    return sample_partner(S, &S->cath[S->inst[inst].cathode], &st, event, rn(w[3]), v, V);
+    return sample_partner(S, &S->cath[S->inst[inst].cathode], &st, event, v, V);
 }
 
 /* repeated collisions in an unbounded gas (no surfaces, no flights): the
@@ -1077,7 +1074,7 @@ void or_thermalize(const or_scene* S, uint64_t seed, int inst, uint64_t pid, dou
     for (int k = 1; k <= n_coll; ++k) {
         draw(&st, (uint32_t)k, 0u, w);
         double V[3], vo[3], Vo[3];
-        sample_partner(S, c, &st, (uint32_t)k, rn(w[3]), v, V);
+        sample_partner(S, c, &st, (uint32_t)k, v, V);
         collide_with(S, c, v, V, rn(w[1]), rn(w[2]), vo, Vo, NULL);
         memcpy(v, vo, sizeof v);
         speeds[k - 1] = sqrt(dot3(v, v));

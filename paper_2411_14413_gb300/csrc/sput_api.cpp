@@ -531,12 +531,14 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.n_abins = S->grid.n_abins;
     p.ebin_per_eV = S->grid.n_ebins > 0 ? (float)(S->grid.n_ebins / S->grid.e_hist_max) : 0.0f;
     // Gauss-Mehler constants: theta_j = (2j-1) pi / (2N), j = 1..N/2
-    for (int j = 0; j < kGMHalf; ++j) {
-        double th = (2.0 * (j + 1) - 1.0) * kPi / (2.0 * kGMNodes);
+    auto gm_node = [](int j, int N) {
+        double th = (2.0 * (j + 1) - 1.0) * kPi / (2.0 * N);
         double c = std::cos(th), s = std::sin(th);
-        p.gm[j] = make_float4((float)c, (float)(1.0 / (1.0 + c)), (float)(c / (s * s)),
-                              (float)(2.0 * std::sin(0.5 * th) * std::sin(0.5 * th) / c));
-    }
+        return make_float4((float)c, (float)(1.0 / (1.0 + c)), (float)(c / (s * s)),
+                           (float)(2.0 * std::sin(0.5 * th) * std::sin(0.5 * th) / c));
+    };
+    for (int j = 0; j < kGMHalf; ++j) p.gm[j] = gm_node(j, kGMNodes);
+    for (int j = 0; j < kGMHalfLo; ++j) p.gm_lo[j] = gm_node(j, kGMNodesLo);
     if (transport_configure((int)S->smem_optin) != 0) {
         sput_scene_destroy(S);
         return fail(SPUT_ERR_CUDA, "cudaFuncSetAttribute on the transport kernel failed");

@@ -66,6 +66,7 @@ struct TableView {
     const float4* bm;
     const float* xh;
     const float4* w;
+    const float4* gm;  // Gauss-Mehler nodes: kGMHalf of the kGMNodes rule, then kGMHalfLo of the kGMNodesLo rule
     const DevPair* pairs;
     int n_bm;
     float bm_lo, bm_inv_h;
@@ -117,10 +118,12 @@ __device__ __forceinline__ float one_minus_exp_neg(float y)
     return 1.0f - expf(-y);
 }
 
-// CM deflection for the Moliere potential in reduced units (eps, beta):
-// apsis by Newton from the head-on lower bound max(beta, x_h), then the
-// Gauss-Mehler sum chi = (2 pi / N) sum_j D_j / (S_j (S_j + beta/x0)).
-__device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
+// CM deflection for the Moliere potential in reduced units (eps, beta), in
+// units of pi: apsis by Newton from the head-on lower bound max(beta, x_h),
+// then the Gauss-Mehler sum chi / pi = (2 / N) sum_j D_j / (S_j (S_j + beta/x0))
+// with N = kGMNodesLo below ln eps = kGMLoLnEps, else kGMNodes (2/N is a power
+// of two, so the scaling is exact).
+__device__ float chi_over_pi_moliere(float eps, float ln_eps, float beta, float xh, const float4* gm)
 {
     const float ie = 1.0f / eps;
     const float b2 = beta * beta;
@@ -138,11 +141,11 @@ __device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
         float e2 = t2 ? kMolC2 * expf(-kMolD2 * x) : 0.0f;
         float ph = e0 + e1 + e2;
         float dph = -(kMolD0 * e0 + kMolD1 * e1 + kMolD2 * e2);
-        float ix = 1.0f / x;
+        float ix = __frcp_rn(x);
         float ix2 = ix * ix;
         float g = 1.0f - b2 * ix2 - ph * ix * ie;
         float gp = 2.0f * b2 * ix2 * ix - (dph * x - ph) * ix2 * ie;
-        x -= g / gp;
+        x -= __fdividef(g, gp);
     }
     const float x0 = x;
     const float bt = beta / x0;
@@ -153,17 +156,23 @@ __device__ float chi_moliere(float eps, float beta, float xh, const float4* gm)
     const float p1 = u1 ? kMolC1 * expf(-kMolD1 * x0) * iex : 0.0f;
     const float p2 = u2 ? kMolC2 * expf(-kMolD2 * x0) * iex : 0.0f;
     const float y0 = kMolD0 * x0, y1 = kMolD1 * x0, y2 = kMolD2 * x0;
+    const bool lo = ln_eps < kGMLoLnEps;
+    const float4* nodes = lo ? gm + kGMHalf : gm;
+    const int nh = lo ? kGMHalfLo : kGMHalf;
     float s = 0.0f;
 #pragma unroll 1
-    for (int j = 0; j < kGMHalf; ++j) {
-        const float4 nd = gm[j];  // (u, 1/(1+u), u/(1-u^2), 1/u - 1)
+    for (int j = 0; j < nh; ++j) {
+        const float4 nd = nodes[j];  // (u, 1/(1+u), u/(1-u^2), 1/u - 1)
         float D = p0 * fmaf(nd.z, one_minus_exp_neg(y0 * nd.w), nd.y);
         if (u1) D = fmaf(p1, fmaf(nd.z, one_minus_exp_neg(y1 * nd.w), nd.y), D);
         if (u2) D = fmaf(p2, fmaf(nd.z, one_minus_exp_neg(y2 * nd.w), nd.y), D);
-        float S = sqrtf(bt2 + D);
-        s += D / (S * (S + bt));
+        // S = sqrt(q), q = (beta/x0)^2 + D > 0; approximate reciprocal square root
+        // and division (2 ulp) are well inside the quadrature error
+        const float q = bt2 + D;
+        const float S = q * rsqrtf(q);
+        s += __fdividef(D, S * (S + bt));
     }
-    return s * (6.283185307179586f / (float)kGMNodes);
+    return s * (lo ? 2.0f / (float)kGMNodesLo : 2.0f / (float)kGMNodes);
 }
 
 // orthonormal pair perpendicular to unit n (Duff et al., JCGT 6(1), 2017)
@@ -331,8 +340,8 @@ struct StepOut {
 
 // Free flight k+1 of the atom in S and the surface test.  Landing: S keeps the
 // pre-flight position and out.t is the hit distance.  Otherwise the atom moves
-// to the collision point; w is the flight's Philox block (impact parameter,
-// azimuth and first acceptance word are used by the collision).
+// to the collision point; w is the flight's Philox block (words 1 and 2, the
+// impact parameter and azimuth, are used by the collision; word 3 is unused).
 __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
                            StepOut& out, uint4& w)
 {
@@ -398,15 +407,17 @@ __device__ __forceinline__ int nth_set_bit(unsigned mask, int n)
 }
 
 // Gas partners of every lane with `need`, drawn by the whole warp: the
-// Maxwellian weighted by sigma(g) g by rejection against M(v), attempt a of a
-// particle from its own Philox block (1 + a) and acceptance word, the first
-// accepted attempt kept (attempt A-1 if none is).  Each round spreads the
-// pending particles' next attempts over all 32 lanes (m consecutive attempts
-// per particle), so the result is the sequential rejection loop's result while
-// the lanes stay busy.  Must be called by all 32 lanes together.
+// Maxwellian weighted by sigma(g) g by rejection against M(v).  Attempt a of a
+// particle uses its own Philox block 1 + a: the upper 24 bits of the four words
+// give the three Box-Muller components, the low bytes of words 0-2 the
+// acceptance uniform; the first accepted attempt is kept (attempt A-1 if none
+// is).  Each round spreads the pending particles' next attempts over all 32
+// lanes (consecutive attempts per particle, the first 32 mod np particles one
+// more), so the result is the sequential rejection loop's result while every
+// lane stays busy.  Must be called by all 32 lanes together.
 __device__ void partner_sample_warp(bool need, const Params& P, const TableView& T, const DevPair* pairs,
                                     uint32_t pid, uint32_t inst, uint32_t k, int pair, float vx, float vy, float vz,
-                                    float M, uint32_t acc0, float& Vx, float& Vy, float& Vz, int& attempts)
+                                    float M, float& Vx, float& Vy, float& Vz, int& attempts)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -416,11 +427,21 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
     Vx = Vy = Vz = 0.0f;
     attempts = 0;
     while (pending) {
+        // np pending particles share 32 lanes: the first `extra` get m + 1 lanes, the rest m
         const int np = __popc(pending);
         const int m = 32 / np;
-        const int slot = lane / m, j = lane - slot * m;
-        const bool has_job = slot < np;
-        const int owner = has_job ? nth_set_bit(pending, slot) : lane;
+        const int extra = 32 - m * np;
+        const int cut = extra * (m + 1);
+        int slot, j;
+        if (lane < cut) {
+            slot = lane / (m + 1);
+            j = lane - slot * (m + 1);
+        } else {
+            const int r = (lane - cut) / m;
+            slot = extra + r;
+            j = lane - cut - r * m;
+        }
+        const int owner = nth_set_bit(pending, slot);
         const uint32_t o_pid = __shfl_sync(kFull, pid, owner);
         const uint32_t o_inst = __shfl_sync(kFull, inst, owner);
         const uint32_t o_k = __shfl_sync(kFull, k, owner);
@@ -429,12 +450,11 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         const float o_vy = __shfl_sync(kFull, vy, owner);
         const float o_vz = __shfl_sync(kFull, vz, owner);
         const float o_M = __shfl_sync(kFull, M, owner);
-        const uint32_t o_acc0 = __shfl_sync(kFull, acc0, owner);
         const int o_next = __shfl_sync(kFull, next_a, owner);
         const int a = o_next + j;
         bool acc = false;
         float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-        if (has_job && a < A) {
+        if (a < A) {
             const uint4 wn = philox(P.key0, P.key1, o_pid, o_inst, o_k, 1u + (uint32_t)a);
             const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
             const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
@@ -444,15 +464,9 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
             cx = P.s_gas * R0 * c1;
             cy = P.s_gas * R0 * s1;
             cz = P.s_gas * R1 * c3;
-            float ua;
-            if (a == 0) {
-                ua = rn(o_acc0);
-            } else {
-                const uint4 wa =
-                    philox(P.key0, P.key1, o_pid, o_inst, o_k, 1u + (uint32_t)A + (uint32_t)((a - 1) >> 2));
-                const int q = (a - 1) & 3;
-                ua = rn(q == 0 ? wa.x : (q == 1 ? wa.y : (q == 2 ? wa.z : wa.w)));
-            }
+            // low bytes of words 0, 1, 2 as one more 24-bit uniform
+            const uint32_t lowb = ((wn.x & 0xffu) << 24) | ((wn.y & 0xffu) << 16) | ((wn.z & 0xffu) << 8);
+            const float ua = rn(lowb);
             const float gx = o_vx - cx, gy = o_vy - cy, gz = o_vz - cz;
             const float g2 = gx * gx + gy * gy + gz * gz;
             acc = ua * o_M <= h_of_g(T, pairs[o_pair], sqrtf(g2), g2) || a == A - 1;
@@ -463,12 +477,16 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         bool done = false;
         if (is_owner) {
             const int my_slot = __popc(pending & lt);
-            const unsigned range = (m >= 32 ? kFull : ((1u << m) - 1u)) << (my_slot * m);
+            const int my_m = my_slot < extra ? m + 1 : m;
+            const int my_lo = my_slot < extra ? my_slot * (m + 1) : cut + (my_slot - extra) * m;
+            const unsigned range = (my_m >= 32 ? kFull : ((1u << my_m) - 1u)) << my_lo;
             const unsigned hit = accm & range;
             if (hit) {
                 src = __ffs(hit) - 1;
-                first = src - my_slot * m;
+                first = src - my_lo;
                 done = true;
+            } else {
+                next_a += my_m;
             }
         }
         const float sx = __shfl_sync(kFull, cx, src);
@@ -479,8 +497,6 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
             Vy = sy;
             Vz = sz;
             attempts = next_a + first + 1;
-        } else if (is_owner) {
-            next_a += m;
         }
         pending &= ~__ballot_sync(kFull, done);
     }
@@ -496,17 +512,17 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
         const float g = sqrtf(g2);
         const float ig = 1.0f / g;
         const float hx = gx * ig, hy = gy * ig, hz = gz * ig;
-        float chi;
+        float chi_pi;  // deflection / pi
         if (pr.hard_sphere) {
-            chi = 2.0f * acosf(sqrtf(rn(w.y)));
+            chi_pi = acosf(sqrtf(rn(w.y))) * (2.0f / 3.14159265358979f);
         } else {
             const float eps = pr.kappa * g2;
             const float le = logf(eps);
             const float beta = bmax_eval(T, le) * sqrtf(rn(w.y));
-            chi = chi_moliere(eps, beta, xh_eval(T, le), P.gm);
+            chi_pi = chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm);
         }
         float sc, cc, sp, cp;
-        sincosf(chi, &sc, &cc);
+        sincospif(chi_pi, &sc, &cc);
         sincospif(2.0f * rn(w.z), &sp, &cp);
         float3 b1, b2;
         onb(hx, hy, hz, b1, b2);
@@ -542,7 +558,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
     float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
     if (P.gas_thermal) {
         const float M = coll ? wtab_eval(T, pr, pr.M_off, S.speed) : 0.0f;
-        partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, M, w.w, Vx, Vy, Vz,
+        partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, M, Vx, Vy, Vz,
                             out.attempts);
     }
     if (coll) scatter(S, P, T, pr, vx, vy, vz, Vx, Vy, Vz, w);
@@ -551,7 +567,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
 
 // ------------------------------------------------------------- kernel
 struct SmemLayout {
-    size_t prims, geoms, pairs, bm, w, prefix, xh, counters, total;
+    size_t prims, geoms, pairs, bm, w, prefix, xh, gm, counters, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -574,6 +590,8 @@ __host__ __device__ inline SmemLayout smem_layout(const Params& p)
     o = align16(o + sizeof(unsigned long long) * (p.n_inst + 1));
     L.xh = o;
     o = align16(o + sizeof(float) * (p.n_bm + 1));
+    L.gm = o;
+    o = align16(o + sizeof(float4) * (kGMHalf + kGMHalfLo));
     L.counters = o;
     o = align16(o + (p.smem_counters ? sizeof(unsigned int) * (size_t)p.n_inst * (p.max_prims + 1) : 0));
     L.total = o;
@@ -602,6 +620,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     float4* s_w = reinterpret_cast<float4*>(smem + L.w);
     unsigned long long* s_prefix = reinterpret_cast<unsigned long long*>(smem + L.prefix);
     float* s_xh = reinterpret_cast<float*>(smem + L.xh);
+    float4* s_gm = reinterpret_cast<float4*>(smem + L.gm);
     unsigned int* s_cnt = reinterpret_cast<unsigned int*>(smem + L.counters);
 
     copy16(s_prims, P.prims, sizeof(DevPrim) * P.n_prims);
@@ -611,6 +630,8 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     copy16(s_w, P.w_tab, sizeof(float4) * P.n_w_total);
     copy16(s_prefix, P.prefix, sizeof(unsigned long long) * (P.n_inst + 1));
     copy16(s_xh, P.xh_tab, sizeof(float) * (P.n_bm + 1));
+    if (threadIdx.x < kGMHalf) s_gm[threadIdx.x] = P.gm[threadIdx.x];
+    else if (threadIdx.x < kGMHalf + kGMHalfLo) s_gm[threadIdx.x] = P.gm_lo[threadIdx.x - kGMHalf];
     const int n_cnt = P.smem_counters ? P.n_inst * (P.max_prims + 1) : 0;
     for (int i = threadIdx.x; i < n_cnt; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
@@ -619,6 +640,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     T.bm = s_bm;
     T.xh = s_xh;
     T.w = s_w;
+    T.gm = s_gm;
     T.pairs = s_pairs;
     T.n_bm = P.n_bm;
     T.bm_lo = P.bm_lo;
@@ -791,11 +813,16 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
 // ------------------------------------------------------------- probes
 __global__ void probe_kernel(const Params P, int what, int idx, int n, const double* x, double* y)
 {
+    __shared__ float4 s_gm[kGMHalf + kGMHalfLo];
+    if (threadIdx.x < kGMHalf) s_gm[threadIdx.x] = P.gm[threadIdx.x];
+    else if (threadIdx.x < kGMHalf + kGMHalfLo) s_gm[threadIdx.x] = P.gm_lo[threadIdx.x - kGMHalf];
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     TableView T;
     T.bm = P.bm_tab;
     T.xh = P.xh_tab;
     T.w = P.w_tab;
+    T.gm = s_gm;
     T.pairs = P.pairs;
     T.n_bm = P.n_bm;
     T.bm_lo = P.bm_lo;
@@ -842,7 +869,7 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
     if (what == SPUT_PROBE_CHI) {
         const float eps = (float)x[2 * i], beta = (float)x[2 * i + 1];
         const float le = logf(eps);
-        y[i] = chi_moliere(eps, beta, xh_eval(T, le), P.gm);
+        y[i] = 3.141592653589793 * (double)chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm);
     } else if (what == SPUT_PROBE_BMAX) {
         y[i] = bmax_eval(T, logf((float)x[i]));
     } else if (what == SPUT_PROBE_K || what == SPUT_PROBE_M) {
