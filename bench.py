@@ -51,9 +51,11 @@ WORKLOAD = WORKLOADS["quaternary"]
 # with 2e5 particles per cathode); the figure is kept fixed so that frac
 # measures speed against one definition of the work.
 LANE_OPS_PER_COLLISION = 4136.0
-# DRAM bytes (read + write) of one launch, from the capture of the current
-# kernel; None whenever the kernel changed after the capture.
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) of one launch of the quaternary workload, from the
+# one-pass capture of the current kernel (mean of 5 launches: 3.82 MB read,
+# 17.07 MB written, most of it the write-back of the dirty L2 lines left by the
+# flush buffer); None whenever the kernel changed after the capture.
+TRAFFIC_PER_LAUNCH = 2.089e7
 LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes issue one instruction per clock each
 
 
@@ -348,7 +350,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "seed": "distinct per step and per rank", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
+                     "frac": achieved / peak,
+                     "traffic": TRAFFIC_PER_LAUNCH if (args.workload == "quaternary" and args.particles == 10_000_000) else None,
                      "kernel": "transport_kernel", "kernel_ms_mean": statistics.mean(kernel_ms),
                      "lane_ops_per_collision": LANE_OPS_PER_COLLISION,
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz)"},

@@ -23,6 +23,9 @@ namespace sput {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// dead lanes of a warp that trigger a refill (measured optimum 4-8 on the
+// quaternary workload; 1 = refill every flight)
+constexpr int kRefillMin = 6;
 
 // ----------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
@@ -428,16 +431,19 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
     attempts = 0;
     while (pending) {
         // np pending particles share 32 lanes: the first `extra` get m + 1 lanes, the rest m
+        // (small-integer quotients through a correctly rounded reciprocal: 32/np
+        // is exact as np <= 32 divides 32 only as a power of two, and
+        // (l + 1/2)/d stays at least 1/66 away from an integer for l < 32, d <= 33)
         const int np = __popc(pending);
-        const int m = 32 / np;
+        const int m = (int)(32.0f * __frcp_rn((float)np));
         const int extra = 32 - m * np;
         const int cut = extra * (m + 1);
         int slot, j;
         if (lane < cut) {
-            slot = lane / (m + 1);
+            slot = (int)(((float)lane + 0.5f) * __frcp_rn((float)(m + 1)));
             j = lane - slot * (m + 1);
         } else {
-            const int r = (lane - cut) / m;
+            const int r = (int)(((float)(lane - cut) + 0.5f) * __frcp_rn((float)m));
             slot = extra + r;
             j = lane - cut - r * m;
         }
@@ -664,8 +670,11 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
 
     for (;;) {
         // ---------------------------------------------------- refill (warp-uniform)
+        // Dead lanes wait until kRefillMin of them (or the whole warp) can be
+        // refilled together: one pass of the launch code then serves several
+        // lanes, which costs less than the lanes' few idle flights.
         const unsigned need = __ballot_sync(kFull, !alive);
-        if (need) {
+        if (need && (__popc(need) >= kRefillMin || need == kFull)) {
             const unsigned n = __popc(need);
             const unsigned rank = __popc(need & lane_lt);
             const unsigned long long avail = pool_end - pool_next;
