@@ -203,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
     import paper_2411_14413_gb300 as pkg
     import workloads
     from paper_2411_14413_gb300 import _native as N
-    from paper_2411_14413_gb300 import api
+    from paper_2411_14413_gb300 import api, shard
 
     dist = None
     if world > 1:
@@ -312,17 +312,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_t = time.perf_counter() - t0
 
     # max over ranks of the time, sum over ranks of the work
-    vec = torch.tensor([total_ms, coll, landed, e2e_t, e2e_coll], dtype=torch.float64, device=dev)
-    if dist is not None:
-        tmax = vec.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = vec.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms_all, e2e_t_all = tmax[0].item(), tmax[3].item()
-        coll_all, landed_all, e2e_coll_all = tsum[1].item(), tsum[2].item(), tsum[4].item()
-    else:
-        total_ms_all, e2e_t_all = total_ms, e2e_t
-        coll_all, landed_all, e2e_coll_all = coll, landed, e2e_coll
+    total_ms_all, (coll_all, landed_all) = shard.reduce_job(total_ms, [coll, landed], device=dev)
+    e2e_t_all, (e2e_coll_all,) = shard.reduce_job(e2e_t, [e2e_coll], device=dev)
     tr.close()
     if rank != 0:
         return
