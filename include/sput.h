@@ -64,7 +64,7 @@
 extern "C" {
 #endif
 
-#define SPUT_ABI_VERSION 1
+#define SPUT_ABI_VERSION 2
 
 typedef enum sput_status {
     SPUT_OK = 0,
@@ -129,6 +129,17 @@ typedef struct sput_cathode {
     double rt_r0, rt_sigma, rt_R;       /* racetrack depth d(r) = exp(-(r-r0)^2/(2 sigma^2)) on [0, R];
                                             radial pdf proportional to r d(r) (axisymmetric profile) */
     double cos_coef[6];          /* c_0..c_5 of the emission cosine sum; (0,1,0,0,0,0) = cosine */
+    /* Optional joint launch distribution in (polar cosine, energy), e.g. binned output of a
+     * binary-collision code for the target (angle-dependent energy distributions, Sec. "The
+     * SIMTRA model").  launch_table[i * n_E + k] >= 0 is the weight of the cell
+     * mu = cos(theta) in [i, i+1) / n_mu and E in [k, k+1) * E_hi / n_E, with a uniform density
+     * inside each cell.  The polar cosine is drawn from the marginal over mu (launch word u_mu),
+     * the energy from the row of the drawn mu cell (word u_E); Thompson law, E_i, k and
+     * cos_coef are then not used for this cathode.  NULL = off.  Copied during
+     * sput_scene_create; 1 <= n_mu, n_E <= 256, E_hi > 0, weights finite, sum > 0. */
+    const double* launch_table;
+    int n_mu, n_E;
+    double E_hi;                 /* eV, upper end of the table's energy range */
 } sput_cathode;
 
 typedef struct sput_instance {   /* one (cathode, process condition) pair */

@@ -106,6 +106,10 @@ def lib():
             L.or_launch.argtypes = [p, u64, i, u64, p, p, p]
             L.or_philox.restype = None
             L.or_philox.argtypes = [p, p, p]
+            L.or_set_launch_table.restype = i
+            L.or_set_launch_table.argtypes = [p, i, i, i, d, p]
+            L.or_table_launch.restype = None
+            L.or_table_launch.argtypes = [p, i, d, d, p, p]
             L.or_version.restype = i
             _lib = L
     return _lib
@@ -172,6 +176,15 @@ class OracleScene:
                                 len(cath), _ptr(cath), len(inst), _ptr(inst), _ptr(grid), _ptr(phys))
         if not self.h:
             raise RuntimeError("or_scene_new failed")
+        self._tables = []
+        for ci, c in enumerate(scene.cathodes):
+            lt = c.get("launch_table")
+            if lt is None:
+                continue
+            w = np.ascontiguousarray(lt["weights"], dtype=np.float64)
+            self._tables.append(w)
+            if L.or_set_launch_table(self.h, ci, w.shape[0], w.shape[1], float(lt["E_hi"]), _ptr(w)) != 0:
+                raise RuntimeError("or_set_launch_table failed")
 
     def close(self):
         if getattr(self, "h", None):
@@ -274,6 +287,12 @@ class OracleScene:
         seed = self.scene.seed if seed is None else seed
         lib().or_trace(self.h, int(seed), int(inst), int(pid), int(rows), _ptr(out))
         return out.reshape(rows, 10)
+
+    def table_launch(self, cath, u_mu, u_E):
+        """(mu, E) drawn from cathode cath's joint launch table for uniforms (u_mu, u_E)."""
+        mu, E = C.c_double(), C.c_double()
+        lib().or_table_launch(self.h, int(cath), float(u_mu), float(u_E), C.byref(mu), C.byref(E))
+        return mu.value, E.value
 
     def launch(self, inst, pid, seed=None):
         p, d, E = np.zeros(3), np.zeros(3), np.zeros(1)

@@ -405,6 +405,11 @@ typedef struct {
     double zze2;    /* Z1 Z2 e^2, eV*Angstrom */
     double mu_red;  /* u */
     int h_monotone; /* sigma(g) g non-decreasing on the checked range */
+    /* optional joint launch table: weights lt[i * n_E + k] of the cells mu in [i, i+1)/n_mu,
+     * E in [k, k+1) E_hi/n_E (uniform inside a cell); NULL = Thompson law + cosine sum */
+    int n_mu, n_E;
+    double E_hi;
+    double* lt;
 } cath_t;
 
 typedef struct {
@@ -733,6 +738,72 @@ static int sample_partner(const or_scene* S, const cath_t* c, const stream_t* st
     return A;
 }
 
+/* Joint launch table: mu from the marginal over the mu cells (uniform u_mu),
+ * then E from the weights of the drawn mu cell (uniform u_E); each draw is the
+ * inverse of the piecewise-linear CDF of a piecewise-uniform density, found by
+ * a plain scan over the cumulative weights (u in ]0,1]). */
+static void table_draw(const double* w, int n, int stride, double u, int* cell, double* t)
+{
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) tot += w[(size_t)i * stride];
+    double target = u * tot, acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double wi = w[(size_t)i * stride];
+        if (wi > 0.0 && acc + wi >= target) {
+            *cell = i;
+            *t = (target - acc) / wi;
+            if (*t > 1.0) *t = 1.0;
+            if (*t < 0.0) *t = 0.0;
+            return;
+        }
+        acc += wi;
+    }
+    /* rounding left u * tot above the sum: the last cell of positive weight */
+    for (int i = n - 1; i >= 0; --i)
+        if (w[(size_t)i * stride] > 0.0) {
+            *cell = i;
+            *t = 1.0;
+            return;
+        }
+    *cell = 0;
+    *t = 1.0;
+}
+
+static void table_launch(const cath_t* c, double u_mu, double u_E, double* mu, double* E)
+{
+    /* marginal weight of mu cell i = sum over k of lt[i][k] */
+    double* row = (double*)malloc((size_t)c->n_mu * sizeof(double));
+    for (int i = 0; i < c->n_mu; ++i) {
+        row[i] = 0.0;
+        for (int k = 0; k < c->n_E; ++k) row[i] += c->lt[(size_t)i * c->n_E + k];
+    }
+    int i, k;
+    double tm, te;
+    table_draw(row, c->n_mu, 1, u_mu, &i, &tm);
+    free(row);
+    table_draw(c->lt + (size_t)i * c->n_E, c->n_E, 1, u_E, &k, &te);
+    *mu = (i + tm) / c->n_mu;
+    *E = (k + te) * c->E_hi / c->n_E;
+}
+
+int or_set_launch_table(or_scene* S, int cath, int n_mu, int n_E, double E_hi, const double* w)
+{
+    if (cath < 0 || cath >= S->n_cath || n_mu < 1 || n_E < 1 || !(E_hi > 0.0)) return -1;
+    cath_t* c = &S->cath[cath];
+    free(c->lt);
+    c->lt = (double*)malloc((size_t)n_mu * n_E * sizeof(double));
+    memcpy(c->lt, w, (size_t)n_mu * n_E * sizeof(double));
+    c->n_mu = n_mu;
+    c->n_E = n_E;
+    c->E_hi = E_hi;
+    return 0;
+}
+
+void or_table_launch(const or_scene* S, int cath, double u_mu, double u_E, double* mu, double* E)
+{
+    table_launch(&S->cath[cath], u_mu, u_E, mu, E);
+}
+
 /* ------------------------------------------------------------- transport */
 typedef struct {
     int32_t prim;  /* local primitive index, -1 = timed out */
@@ -772,8 +843,12 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
     draw(&st, 0u, 0u, w);
     double r = or_racetrack_r(c->rt_r0, c->rt_sigma, c->rt_R, rn(w[0]));
     double al = 2.0 * M_PI * rn(w[1]);
-    double E = or_thompson(I->E_max, c->U_s, rn(w[2]));
-    double mu = or_cos_mu(c->coef, rn(w[3]));
+    double E, mu;
+    if (c->lt) table_launch(c, rn(w[3]), rn(w[2]), &mu, &E);
+    else {
+        E = or_thompson(I->E_max, c->U_s, rn(w[2]));
+        mu = or_cos_mu(c->coef, rn(w[3]));
+    }
     draw(&st, 0u, 1u, w);
     double ph = 2.0 * M_PI * rn(w[0]);
     double st_ = sqrt((1.0 - mu) * (1.0 + mu));
@@ -970,6 +1045,7 @@ void or_scene_free(or_scene* S)
     if (!S) return;
     free(S->prims);
     free(S->geoms);
+    for (int i = 0; i < S->n_cath; ++i) free(S->cath[i].lt);
     free(S->cath);
     free(S->inst);
     free(S);
@@ -1091,8 +1167,12 @@ void or_launch(const or_scene* S, uint64_t seed, int ii, uint64_t pid, double* p
     draw(&st, 0u, 0u, w);
     double r = or_racetrack_r(c->rt_r0, c->rt_sigma, c->rt_R, rn(w[0]));
     double al = 2.0 * M_PI * rn(w[1]);
-    *E = or_thompson(I->E_max, c->U_s, rn(w[2]));
-    double mu = or_cos_mu(c->coef, rn(w[3]));
+    double mu;
+    if (c->lt) table_launch(c, rn(w[3]), rn(w[2]), &mu, E);
+    else {
+        *E = or_thompson(I->E_max, c->U_s, rn(w[2]));
+        mu = or_cos_mu(c->coef, rn(w[3]));
+    }
     draw(&st, 0u, 1u, w);
     double ph = 2.0 * M_PI * rn(w[0]);
     double s = sqrt((1.0 - mu) * (1.0 + mu));

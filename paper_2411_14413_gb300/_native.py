@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # --------------------------------------------------------------- ABI mirror
-SPUT_ABI_VERSION = 1
+SPUT_ABI_VERSION = 2
 SPUT_OK = 0
 STATUS_NAMES = {0: "SPUT_OK", 1: "SPUT_ERR_INVALID_ARG", 2: "SPUT_ERR_INVALID_SCENE", 3: "SPUT_ERR_CUDA",
                 4: "SPUT_ERR_TIMEOUT", 5: "SPUT_ERR_DEVICE_CHECK", 6: "SPUT_ERR_UNSUPPORTED", 7: "SPUT_ERR_NO_MEMORY"}
@@ -105,7 +105,8 @@ class sput_cathode(C.Structure):
     _fields_ = [("Z", C.c_int), ("target", C.c_int), ("mass", C.c_double), ("U_s", C.c_double),
                 ("center", D3), ("normal", D3), ("e1", D3),
                 ("rt_r0", C.c_double), ("rt_sigma", C.c_double), ("rt_R", C.c_double),
-                ("cos_coef", C.c_double * 6)]
+                ("cos_coef", C.c_double * 6),
+                ("launch_table", C.POINTER(C.c_double)), ("n_mu", C.c_int), ("n_E", C.c_int), ("E_hi", C.c_double)]
 
 
 class sput_instance(C.Structure):

@@ -24,6 +24,7 @@ def _lib():
 # ----------------------------------------------------------- marshalling
 def scene_desc(scene):
     """Build the sput_scene_desc (and keep the arrays it points to alive)."""
+    keep = []
     prims = (N.sput_primitive * len(scene.prims))()
     for i, P in enumerate(scene.prims):
         q = prims[i]
@@ -48,6 +49,15 @@ def scene_desc(scene):
         q.e1[:] = c["e1"]
         q.rt_r0, q.rt_sigma, q.rt_R = rt["r0"], rt["sigma"], rt["R"]
         q.cos_coef[:] = c["cos_coef"]
+        lt = c.get("launch_table")
+        if lt is not None:
+            w = np.ascontiguousarray(lt["weights"], dtype=np.float64)
+            if w.ndim != 2:
+                raise ValueError("launch_table weights must be a 2-D array [n_mu][n_E]")
+            keep.append(w)
+            q.launch_table = w.ctypes.data_as(C.POINTER(C.c_double))
+            q.n_mu, q.n_E = w.shape
+            q.E_hi = float(lt["E_hi"])
     inst = instance_array(scene)
     d = N.sput_scene_desc()
     d.abi_version = N.SPUT_ABI_VERSION
@@ -72,7 +82,7 @@ def scene_desc(scene):
     d.physics.gas_motion = N.GAS_MOTION[ph["gas_motion"]]
     d.physics.max_attempts = ph["max_attempts"]
     d.physics.max_collisions = ph["max_collisions"]
-    return d, (prims, geoms, cath, inst)
+    return d, (prims, geoms, cath, inst, keep)
 
 
 def instance_array(scene):

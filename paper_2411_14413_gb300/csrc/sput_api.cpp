@@ -96,6 +96,8 @@ struct sput_scene {
     std::vector<unsigned long long> prefix;
     std::vector<float4> wtab;
     std::vector<float4> rt;
+    std::vector<std::vector<double>> lt_weights;  // copies of the cathodes' joint launch tables
+    std::vector<float> lt;                        // their CDFs (DevCathode::lt_off)
     std::vector<PairPhys> pair_phys;
     std::vector<int> pair_monotone;
     std::vector<double> pair_E_top;
@@ -106,7 +108,7 @@ struct sput_scene {
     // device memory
     unsigned char* d_blob = nullptr;
     size_t off_prims = 0, off_geoms = 0, off_cath = 0, off_pairs = 0, off_inst = 0, off_prefix = 0, off_bm = 0,
-           off_xh = 0, off_w = 0, off_rt = 0, blob_bytes = 0;
+           off_xh = 0, off_w = 0, off_rt = 0, off_lt = 0, blob_bytes = 0;
     // run scratch (allocated on the first run): ticket counter, stats, status word
     unsigned long long* d_scratch = nullptr;
     unsigned long long* h_scratch = nullptr;  // pinned
@@ -173,6 +175,18 @@ sput_status validate(const sput_scene_desc* d)
             sum += C.cos_coef[i];
         }
         if (!(sum > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "cosine coefficients must not all be zero");
+        if (C.launch_table) {
+            if (C.n_mu < 1 || C.n_mu > 256 || C.n_E < 1 || C.n_E > 256)
+                return fail(SPUT_ERR_INVALID_SCENE, "launch table needs 1 <= n_mu, n_E <= 256");
+            if (!(C.E_hi > 0.0) || !std::isfinite(C.E_hi)) return fail(SPUT_ERR_INVALID_SCENE, "launch table needs E_hi > 0");
+            double tot = 0.0;
+            for (int i = 0; i < C.n_mu * C.n_E; ++i) {
+                const double w = C.launch_table[i];
+                if (!(w >= 0.0) || !std::isfinite(w)) return fail(SPUT_ERR_INVALID_SCENE, "launch table weights must be finite and >= 0");
+                tot += w;
+            }
+            if (!(tot > 0.0) || !std::isfinite(tot)) return fail(SPUT_ERR_INVALID_SCENE, "launch table weights must not all be zero");
+        }
     }
     const sput_grid& gr = d->grid;
     if (gr.nx < 1 || gr.ny < 1 || !(gr.half_u > 0.0) || !(gr.half_v > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "grid needs nx, ny >= 1 and positive extent");
@@ -246,7 +260,7 @@ static sput_status pack_instances(sput_scene* S)
         double Em = thompson_emax(I.k, S->chamber.gas_mass, C.mass, I.E_i, C.U_s);
         if (!(Em > 0.0)) return fail(SPUT_ERR_INVALID_SCENE, "E_max = k Lambda E_i - U_s must be > 0");
         int pair = S->dcath[I.cathode].pair;
-        if (Em > S->pair_E_top[pair] * (1.0 + 1e-12))
+        if (!C.launch_table && Em > S->pair_E_top[pair] * (1.0 + 1e-12))
             return fail(SPUT_ERR_INVALID_ARG, "E_max beyond the range of the scene's tables; recreate the scene");
         DevInstance& D = S->dinst[i];
         D.geometry = I.geometry;
@@ -291,6 +305,12 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->prims.assign(desc->prims, desc->prims + desc->n_prims);
     S->geoms.assign(desc->geoms, desc->geoms + desc->n_geoms);
     S->cathodes.assign(desc->cathodes, desc->cathodes + desc->n_cathodes);
+    S->lt_weights.resize(S->cathodes.size());
+    for (size_t c = 0; c < S->cathodes.size(); ++c) {
+        sput_cathode& C = S->cathodes[c];
+        if (C.launch_table) S->lt_weights[c].assign(C.launch_table, C.launch_table + (size_t)C.n_mu * C.n_E);
+        C.launch_table = S->lt_weights[c].empty() ? nullptr : S->lt_weights[c].data();
+    }
     S->instances.assign(desc->instances, desc->instances + desc->n_instances);
 
     const bool hard = S->physics.interaction == SPUT_INTERACTION_HARD_SPHERE;
@@ -358,7 +378,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     }
     for (const sput_instance& I : S->instances) {
         const sput_cathode& C = S->cathodes[I.cathode];
-        double Em = thompson_emax(I.k, S->chamber.gas_mass, C.mass, I.E_i, C.U_s);
+        // highest launch energy: the Thompson cut-off, or the table's upper end
+        double Em = C.launch_table ? C.E_hi : thompson_emax(I.k, S->chamber.gas_mass, C.mass, I.E_i, C.U_s);
         double& top = S->pair_E_top[cath_pair[I.cathode]];
         top = std::max(top, std::max(2.0 * Em, 200.0));
     }
@@ -404,7 +425,39 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
             D.e2[a] = (float)e2[a];
         }
         D.rt_R = (float)C.rt_R;
-        for (int q = 0; q < 11; ++q) D.rt_pad[q] = 0.0f;
+        for (int q = 0; q < 7; ++q) D.rt_pad[q] = 0.0f;
+        D.lt_off = -1;
+        D.lt_nmu = D.lt_nE = 0;
+        D.lt_dE = 0.0f;
+        if (C.launch_table) {
+            // marginal CDF over mu cells, then one conditional CDF over E per mu cell
+            const int nm = C.n_mu, ne = C.n_E;
+            D.lt_off = (int)S->lt.size();
+            D.lt_nmu = nm;
+            D.lt_nE = ne;
+            D.lt_dE = (float)(C.E_hi / ne);
+            std::vector<double> row(nm, 0.0);
+            double tot = 0.0;
+            for (int i = 0; i < nm; ++i) {
+                for (int k = 0; k < ne; ++k) row[i] += C.launch_table[(size_t)i * ne + k];
+                tot += row[i];
+            }
+            double acc = 0.0;
+            S->lt.push_back(0.0f);
+            for (int i = 0; i < nm; ++i) {
+                acc += row[i];
+                S->lt.push_back(i + 1 == nm ? 1.0f : (float)(acc / tot));
+            }
+            for (int i = 0; i < nm; ++i) {
+                double a2 = 0.0;
+                S->lt.push_back(0.0f);
+                for (int k = 0; k < ne; ++k) {
+                    a2 += C.launch_table[(size_t)i * ne + k];
+                    // a row of zero weight is never drawn; give it a valid ramp
+                    S->lt.push_back(k + 1 == ne ? 1.0f : (float)(row[i] > 0.0 ? a2 / row[i] : (k + 1.0) / ne));
+                }
+            }
+        }
         double norm = 0.0;
         bool pure = true;
         for (int i = 0; i < 6; ++i) {
@@ -462,6 +515,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->off_xh = place(sizeof(float) * xh.size());
     S->off_w = place(sizeof(float4) * S->wtab.size());
     S->off_rt = place(sizeof(float4) * S->rt.size());
+    S->off_lt = place(sizeof(float) * S->lt.size());
     S->blob_bytes = o;
     cudaError_t e = cudaMalloc(&S->d_blob, S->blob_bytes);
     if (e != cudaSuccess) {
@@ -482,6 +536,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     put(S->off_xh, xh.data(), sizeof(float) * xh.size());
     put(S->off_w, S->wtab.data(), sizeof(float4) * S->wtab.size());
     put(S->off_rt, S->rt.data(), sizeof(float4) * S->rt.size());
+    put(S->off_lt, S->lt.data(), sizeof(float) * S->lt.size());
     e = cudaMemcpy(S->d_blob, h.data(), S->blob_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_scratch, 64);
     if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
@@ -503,6 +558,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.xh_tab = reinterpret_cast<const float*>(S->d_blob + S->off_xh);
     p.w_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_w);
     p.rt_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_rt);
+    p.lt_tab = reinterpret_cast<const float*>(S->d_blob + S->off_lt);
     p.n_prims = (int)S->dprims.size();
     p.n_geoms = (int)S->dgeoms.size();
     p.n_pairs = (int)S->dpairs.size();

@@ -58,7 +58,12 @@ struct alignas(16) DevCathode {
     float c[3], n[3], e1[3], e2[3];
     // racetrack: inverse radial CDF as cubic pieces, rt_n per half (see rt_tab of Params)
     float rt_R;
-    float rt_pad[11];
+    // joint (mu, E) launch table: float offset in Params::lt_tab of the marginal CDF over
+    // lt_nmu cells of mu (lt_nmu + 1 values) followed by lt_nmu conditional CDFs over
+    // lt_nE energy cells (lt_nE + 1 values each); lt_off < 0 = Thompson law + cosine sum
+    int lt_off, lt_nmu, lt_nE;
+    float lt_dE;                           // eV per energy cell
+    float rt_pad[7];
     float coef[6];
     float coef_norm;                       // sum c_i/(i+1)
     int cos_general;                       // 0 = pure cosine (mu = sqrt(u))
@@ -109,6 +114,7 @@ struct Params {
     const float* xh_tab;               // n_bm + 1 head-on apsis values (linear)
     const float4* w_tab;               // all pairs' K and M pieces
     const float4* rt_tab;              // racetrack inverse-CDF pieces (2 rt_n per cathode)
+    const float* lt_tab;               // joint launch-table CDFs (see DevCathode::lt_off)
     int n_prims, n_geoms, n_pairs, n_inst;
     int n_bm, n_w_total;
     float bm_lo, bm_inv_h;

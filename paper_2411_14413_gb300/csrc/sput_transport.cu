@@ -231,6 +231,23 @@ __device__ float cosine_sum_mu(const DevCathode& C, float u)
     return 0.5f * (lo + hi);
 }
 
+// Inverse CDF of a piecewise-uniform density over n cells: F[0..n] the
+// cumulative weights (F[0] = 0, F[n] = 1), u in ]0,1].  Returns the first cell
+// i with F[i+1] >= u (cells of zero weight are never returned) and the position
+// t in ]0,1] of u inside it.
+__device__ int table_pick(const float* F, int n, float u, float& t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (F[mid + 1] >= u) hi = mid;
+        else lo = mid + 1;
+    }
+    const float f0 = F[lo], d = F[lo + 1] - f0;
+    t = d > 0.0f ? fminf(fmaxf((u - f0) / d, 0.0f), 1.0f) : 1.0f;
+    return lo;
+}
+
 __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t inst, uint32_t pid, float& px,
                              float& py, float& pz, float& dx, float& dy, float& dz, float& E)
 {
@@ -241,9 +258,20 @@ __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t ins
     const float r = racetrack_r(C, rt_tab, P.rt_n, rn(w0.x));
     float sa, ca;
     sincospif(2.0f * rn(w0.y), &sa, &ca);
-    const float s = sqrtf(rn(w0.z)) * I.thompson_q;
-    E = I.U_s * s / (1.0f - s);
-    const float mu = cosine_sum_mu(C, rn(w0.w));
+    float mu;
+    if (C.lt_off >= 0) {
+        // joint table: mu from the marginal (word 3), E from the drawn row (word 2)
+        const float* F = P.lt_tab + C.lt_off;
+        float tm, te;
+        const int i = table_pick(F, C.lt_nmu, rn(w0.w), tm);
+        const int k = table_pick(F + (C.lt_nmu + 1) + i * (C.lt_nE + 1), C.lt_nE, rn(w0.z), te);
+        mu = ((float)i + tm) / (float)C.lt_nmu;
+        E = ((float)k + te) * C.lt_dE;
+    } else {
+        const float s = sqrtf(rn(w0.z)) * I.thompson_q;
+        E = I.U_s * s / (1.0f - s);
+        mu = cosine_sum_mu(C, rn(w0.w));
+    }
     float sp, cp;
     sincospif(2.0f * rn(w1.x), &sp, &cp);
     const float st = sqrtf((1.0f - mu) * (1.0f + mu));

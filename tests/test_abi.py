@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import workloads
@@ -53,7 +54,8 @@ int main(void) {
   S(sput_run_stats) S(sput_tune_result)
   O(sput_tune_result, cand_rate) O(sput_run_opts, flags)
   O(sput_scene_desc, chamber) O(sput_scene_desc, prims) O(sput_scene_desc, grid) O(sput_scene_desc, physics)
-  O(sput_cathode, rt_r0) O(sput_cathode, cos_coef) O(sput_instance, n_particles) O(sput_grid, e_hist_max)
+  O(sput_cathode, rt_r0) O(sput_cathode, cos_coef) O(sput_cathode, launch_table) O(sput_cathode, n_E)
+  O(sput_cathode, E_hi) O(sput_instance, n_particles) O(sput_grid, e_hist_max)
   O(sput_physics, max_collisions) O(sput_run_opts, timeout_ms) O(sput_run_stats, kernel_ms)
   O(sput_tally_layout, n_tickets) O(sput_record, score)
   return 0;
@@ -98,6 +100,11 @@ def _create(scene):
     (lambda s: s.instances[0].__setitem__("E_i", -5.0), 2),
     (lambda s: s.instances[0].__setitem__("n", 2**32), 2),
     (lambda s: s.cathodes[0].__setitem__("target", 2), 2),
+    (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.zeros((4, 4)), "E_hi": 100.0}), 2),
+    (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": -np.ones((4, 4)), "E_hi": 100.0}), 2),
+    (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.ones((4, 4)), "E_hi": 0.0}), 2),
+    (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.ones((300, 4)), "E_hi": 100.0}), 2),
+    (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.full((4, 4), np.nan), "E_hi": 100.0}), 2),
 ])
 def test_host_validation_rejects_bad_scenes(lib, mutate, expect):
     """Invalid descriptions fail in host validation, before any CUDA call."""

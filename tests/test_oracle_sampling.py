@@ -170,3 +170,79 @@ def test_racetrack_cdf_and_moments(oracle_mod):
     assert abs((rr**2).mean() - m2_want) < 5e-3
     assert rr.min() >= 0 and rr.max() <= R
     assert abs(oracle_mod.racetrack_r(r0, sg, R, 1.0) - R) < 1e-9
+
+
+# ------------------------------------------------- joint (mu, E) launch table
+def _table_scene(weights, E_hi):
+    return workloads.scene_single_ni_table(n=1, table={"weights": np.asarray(weights, float), "E_hi": E_hi})
+
+
+def _table_samples(oracle_mod, weights, E_hi, n=20000, seed=1):
+    osc = oracle_mod.OracleScene(_table_scene(weights, E_hi))
+    rng = np.random.default_rng(seed)
+    u = 1.0 - rng.random((n, 2))          # ]0, 1]
+    out = np.array([osc.table_launch(0, a, b) for a, b in u])
+    osc.close()
+    return out[:, 0], out[:, 1]
+
+
+def _piecewise_cdf(cell_weights, width):
+    """CDF of the piecewise-uniform density with the given cell weights."""
+    w = np.asarray(cell_weights, float)
+    F = np.concatenate([[0.0], np.cumsum(w)]) / w.sum()
+
+    def cdf(x):
+        j = np.clip((np.asarray(x) / width).astype(int), 0, len(w) - 1)
+        t = np.clip(np.asarray(x) / width - j, 0.0, 1.0)
+        return F[j] + t * (F[j + 1] - F[j])
+    return cdf
+
+
+def test_launch_table_uniform_table_gives_uniform_mu_and_E(oracle_mod):
+    mu, E = _table_samples(oracle_mod, np.ones((8, 16)), 100.0)
+    assert stats.kstest(mu, "uniform").pvalue > 1e-3
+    assert stats.kstest(E / 100.0, "uniform").pvalue > 1e-3
+    assert abs(np.corrcoef(mu, E)[0, 1]) < 4 / math.sqrt(len(mu))
+
+
+def test_launch_table_single_cell(oracle_mod):
+    w = np.zeros((8, 16))
+    w[3, 5] = 2.5
+    mu, E = _table_samples(oracle_mod, w, 160.0, n=4000)
+    assert np.all((mu > 3 / 8) & (mu <= 4 / 8)) and np.all((E > 50.0) & (E <= 60.0))
+    assert stats.kstest((mu - 3 / 8) * 8, "uniform").pvalue > 1e-3
+    assert stats.kstest((E - 50.0) / 10.0, "uniform").pvalue > 1e-3
+
+
+def test_launch_table_marginals_and_conditional(oracle_mod):
+    """Synthetic table with mu-E correlation: the mu marginal and the E marginal
+    follow the exact piecewise-linear CDFs of the table; the energies drawn in
+    the top and the bottom mu cell have their rows' exact means."""
+    t = workloads.synthetic_launch_table(n_mu=16, n_E=32, E_hi=120.0)
+    w, E_hi = t["weights"], t["E_hi"]
+    mu, E = _table_samples(oracle_mod, w, E_hi, n=30000)
+    assert stats.kstest(mu, _piecewise_cdf(w.sum(1), 1 / 16)).pvalue > 1e-3
+    dE = E_hi / 32
+    # E marginal: mixture over rows of piecewise-uniform densities = piecewise uniform with column sums
+    assert stats.kstest(E, _piecewise_cdf(w.sum(0), dE)).pvalue > 1e-3
+    centres = (np.arange(32) + 0.5) * dE
+    for i in (0, 15):
+        sel = (mu > i / 16) & (mu <= (i + 1) / 16)
+        want = (w[i] * centres).sum() / w[i].sum()
+        second = (w[i] * (centres ** 2 + dE ** 2 / 12)).sum() / w[i].sum()
+        sd = math.sqrt(second - want ** 2)
+        assert abs(E[sel].mean() - want) < 4 * sd / math.sqrt(sel.sum()), (i, E[sel].mean(), want)
+    # the high-energy tail is more forward-peaked than the low-energy part
+    assert mu[E > 60].mean() > mu[E < 5].mean()
+
+
+def test_launch_table_cell_edges(oracle_mod):
+    """u equal to a cumulative weight ends the cell exactly (t = 1); cells of
+    zero weight are never drawn."""
+    w = np.array([[1.0, 0.0, 3.0], [0.0, 0.0, 0.0], [2.0, 2.0, 0.0]])
+    osc = oracle_mod.OracleScene(_table_scene(w, 30.0))
+    mu, E = osc.table_launch(0, 4.0 / 8.0, 0.25)       # end of mu cell 0; E: end of E cell 0
+    assert mu == pytest.approx(1 / 3) and E == pytest.approx(10.0)
+    mu, E = osc.table_launch(0, 4.0 / 8.0 + 1e-9, 1.0)  # just past cell 0 -> cell 2 (cell 1 empty)
+    assert mu > 2 / 3 and E == pytest.approx(20.0)
+    osc.close()

@@ -17,6 +17,8 @@ from .elements import ELEMENTS, GAS_AR, element
 from .scenes import (
     Scene,
     scene_single_ni,
+    scene_single_ni_table,
+    synthetic_launch_table,
     scene_quaternary,
     scene_tilt_pressure_sweep,
     scene_large_shielded,
@@ -29,6 +31,8 @@ __all__ = [
     "element",
     "Scene",
     "scene_single_ni",
+    "scene_single_ni_table",
+    "synthetic_launch_table",
     "scene_quaternary",
     "scene_tilt_pressure_sweep",
     "scene_large_shielded",

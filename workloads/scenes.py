@@ -191,6 +191,29 @@ def scene_single_ni(n=100_000, pressure=0.5, E_i=400.0, T=300.0, nx=50, ny=50,
 
 
 # ---------------------------------------------------------------------------
+# Joint (polar cosine, energy) launch table standing in for the binned output
+# of a binary-collision code for the target: an energy spectrum peaking at a few
+# eV with a power-law tail, whose angular distribution narrows towards the
+# normal as the energy grows (exponent 0.6 at low E, towards 2 at high E).
+# ---------------------------------------------------------------------------
+def synthetic_launch_table(n_mu=32, n_E=64, E_hi=150.0, E_peak=3.0) -> dict:
+    mu = (np.arange(n_mu) + 0.5) / n_mu
+    E = (np.arange(n_E) + 0.5) * E_hi / n_E
+    expo = 0.6 + 1.4 * E / (E + 20.0)
+    w = mu[:, None] ** expo[None, :] * (E / (E + 2.0 * E_peak) ** 2.5)[None, :]
+    return {"weights": w, "E_hi": float(E_hi)}
+
+
+def scene_single_ni_table(n=100_000, table=None, **kw) -> Scene:
+    """The single-Ni scene with its cathode launching from a joint (mu, E) table."""
+    import copy
+    sc = copy.deepcopy(scene_single_ni(n=n, **kw))
+    sc.cathodes[0]["launch_table"] = table if table is not None else synthetic_launch_table()
+    sc.name = "single_ni_table"
+    return sc
+
+
+# ---------------------------------------------------------------------------
 # Quaternary co-sputter Ni/Pd/Pt/Ru: cathodes at azimuth 0/90/180/270 deg,
 # tilted 30 deg, axes meeting at the substrate centre 120 mm from each target;
 # 100 mm wafer, 200x200 int64 counts + fp64 energy per cathode.
@@ -325,6 +348,7 @@ def scene_large_shielded(n=1_000_000_000, pressure=3.0, E_i=400.0, T=300.0, nx=5
 
 _BUILDERS = {
     "single_ni": scene_single_ni,
+    "single_ni_table": scene_single_ni_table,
     "quaternary": scene_quaternary,
     "sweep": scene_tilt_pressure_sweep,
     "large": scene_large_shielded,
