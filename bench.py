@@ -336,6 +336,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "landed_per_s": landed_all / (total_ms_all / 1e3),
         "config": {"workload": WORKLOADS[args.workload], "particles_per_step_per_gpu": sc.total_particles,
+                   "particle_scale": (args.particles / 10_000_000) if args.workload == "sweep" else 1.0,
                    "instances": len(sc.instances), "grid": f"{sc.grid['nx']}x{sc.grid['ny']}",
                    "tallies": "int64 counts + fp64 energy + int64 per-primitive landings",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
@@ -370,7 +371,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--particles", type=int, default=10_000_000, help="per cathode")
+    ap.add_argument("--particles", type=int, default=None,
+                    help="per cathode (quaternary, default 1e7); sweep: counts scaled by particles/1e7 "
+                         "(default 1e6, one tenth, so that a run ends in minutes); large: particles x 100 "
+                         "(default 1e6 -> 1e8)")
     ap.add_argument("--cpu-particles", type=int, default=600, help="oracle sample per cathode")
     ap.add_argument("--ref-particles", type=int, default=400, help="oracle sample per cathode per step")
     ap.add_argument("--no-e2e", action="store_true")
@@ -379,6 +383,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="autotune the launch shape before timing")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-launch-per-instance comparison")
     args = ap.parse_args()
+    if args.particles is None:
+        args.particles = {"quaternary": 10_000_000, "sweep": 1_000_000, "large": 1_000_000}[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
