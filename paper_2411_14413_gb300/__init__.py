@@ -5,7 +5,7 @@ with the thermal gas, tallies) runs in ``libsput.so``, hand-written CUDA for
 sm_103a behind the C ABI of ``include/sput.h``; ``api`` is its Python binding.
 """
 
-from . import _native, shard
+from . import _native, library, shard
 from .api import (
     Transport,
     sput_autotune,

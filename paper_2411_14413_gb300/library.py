@@ -1,0 +1,124 @@
+"""Materials-library analysis of simulated composition maps.
+
+The paper compares the composition range that a simulated library covers with
+the measured one and traces a smaller measured range to a cathode tilt that
+differs from the assumed one (Sec. "Results", the ternary Pd-Pt-Ru library):
+an increased common tilt shrinks the covered compositional area, so the tilt
+can be estimated by simulating the library at several tilts and matching the
+area (and the maps themselves) to the measurement.
+
+* ``composition_maps`` runs a scene whose instances form consecutive libraries
+  (e.g. ``workloads.scene_tilt_scan``: tilt-major, n_el instances per tilt) in
+  ONE transport launch and converts every library's counts to an at.% map with
+  the composition kernel (``sput_composition``).
+* ``compositional_area`` is the share of the composition simplex covered by the
+  convex hull of a map's points (the area of a ternary library in the ternary
+  diagram; a volume share for four elements).
+* ``diagnose_tilt`` estimates the common tilt of a measured map from maps
+  simulated at a range of tilts, by the area criterion and by least squares.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import _native as N
+
+
+def composition_maps(transport, n_el, patch_of_cell, ref_point, calibration, power, seed=None, stream=None):
+    """[n_lib][n_points][n_el] at.% maps (device tensor) of the consecutive
+    libraries of n_el instances in `transport`'s scene, from one run.
+
+    calibration: host [n_el][6] rate-line rows (P_a, R_a, P_b, R_b, density, mass)
+    shared by every library; power: host [n_el] in W."""
+    import torch
+
+    L = transport.layout
+    if L.n_instances % n_el:
+        raise ValueError("the instance count is not a multiple of the library size")
+    n_lib = L.n_instances // n_el
+    dev = torch.device("cuda", transport.device)
+    s = stream if stream is not None else torch.cuda.current_stream(transport.device).cuda_stream
+    transport.run(seed=seed, stream=s, want_stats=False)
+    counts = transport.t["counts"]
+    if counts.dtype != torch.int64:
+        raise ValueError("composition maps need int64 counts")
+    n_cells = L.nx * L.ny
+    patch = torch.as_tensor(np.ascontiguousarray(patch_of_cell, np.int32), device=dev)
+    n_points = int(np.max(patch_of_cell)) + 1
+    cal = np.ascontiguousarray(calibration, dtype=np.float64).reshape(n_el, 6)
+    pw = np.ascontiguousarray(power, dtype=np.float64).reshape(n_el)
+    patch_counts = torch.empty((n_lib, n_el, n_points), dtype=torch.float64, device=dev)
+    comp = torch.empty((n_lib, n_points, n_el), dtype=torch.float64, device=dev)
+    lib = N.load()
+    for t in range(n_lib):
+        rc = lib.sput_composition(n_el, n_cells, n_points,
+                                  C.c_void_p(counts.data_ptr() + t * n_el * n_cells * counts.element_size()),
+                                  C.c_void_p(patch.data_ptr()), int(ref_point), cal.ctypes.data_as(C.c_void_p),
+                                  pw.ctypes.data_as(C.c_void_p), C.c_void_p(patch_counts[t].data_ptr()),
+                                  C.c_void_p(comp[t].data_ptr()), C.c_void_p(s))
+        N.check(rc, "sput_composition")
+    return comp
+
+
+def compositional_area(comp):
+    """Share of the composition simplex covered by the convex hull of the points.
+
+    comp: [n_points][n_el] at.% (rows sum to 100), n_el = 3 or 4.  The points
+    are mapped to the first n_el - 1 atomic fractions, an affine image of the
+    simplex of volume 1/(n_el - 1)!, so the share is hull volume * (n_el - 1)!."""
+    from scipy.spatial import ConvexHull
+
+    x = np.asarray(comp, dtype=np.float64)
+    n_el = x.shape[1]
+    if n_el not in (3, 4):
+        raise ValueError("compositional area is defined here for ternary and quaternary libraries")
+    y = x[:, : n_el - 1] / 100.0
+    return float(ConvexHull(y).volume * math.factorial(n_el - 1))
+
+
+def _parabola_min(x, y):
+    """Abscissa of the minimum of the parabola through the smallest sample and
+    its two neighbours (the end sample itself at an end of the range)."""
+    i = int(np.argmin(y))
+    if i == 0 or i == len(x) - 1:
+        return float(x[i])
+    x0, x1, x2 = x[i - 1], x[i], x[i + 1]
+    y0, y1, y2 = y[i - 1], y[i], y[i + 1]
+    den = (x0 - x1) * (x0 - x2) * (x1 - x2)
+    a = (x2 * (y1 - y0) + x1 * (y0 - y2) + x0 * (y2 - y1)) / den
+    b = (x2 * x2 * (y0 - y1) + x1 * x1 * (y2 - y0) + x0 * x0 * (y1 - y2)) / den
+    return float(-b / (2 * a)) if a > 0 else float(x1)
+
+
+def diagnose_tilt(measured, tilts, simulated):
+    """Common cathode tilt of a measured library map.
+
+    measured: [n_points][n_el] at.%; simulated: [n_tilts][n_points][n_el] at.%
+    at the increasing `tilts` (degrees).  Returns the tilt at which the
+    simulated compositional area equals the measured one (linear interpolation
+    between the bracketing tilts; None when no bracket exists), the tilt of
+    least mean squared composition difference (parabola through the best
+    three), and the per-tilt areas and mean squared differences."""
+    tilts = np.asarray(tilts, dtype=np.float64)
+    sim = np.asarray(simulated, dtype=np.float64)
+    meas = np.asarray(measured, dtype=np.float64)
+    areas = np.array([compositional_area(m) for m in sim])
+    a_meas = compositional_area(meas)
+    mse = ((sim - meas[None]) ** 2).mean(axis=(1, 2))
+    t_area = None
+    for i in range(len(tilts) - 1):
+        a0, a1 = areas[i] - a_meas, areas[i + 1] - a_meas
+        if a0 == 0.0:
+            t_area = float(tilts[i])
+            break
+        if a0 * a1 < 0.0:
+            t_area = float(tilts[i] + (tilts[i + 1] - tilts[i]) * a0 / (a0 - a1))
+            break
+    if t_area is None and areas[-1] == a_meas:
+        t_area = float(tilts[-1])
+    return {"tilt_area": t_area, "tilt_lsq": _parabola_min(tilts, mse), "area_measured": a_meas,
+            "areas": areas.tolist(), "mse": mse.tolist()}

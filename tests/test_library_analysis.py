@@ -1,0 +1,69 @@
+"""Host-side library analysis: the compositional area against closed forms
+and a brute-force hull, and the tilt estimate on maps with a known answer."""
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2411_14413_gb300 import library
+
+
+def _gift_wrap_area(p):
+    """Area of the convex hull of 2-D points by gift wrapping + shoelace."""
+    p = np.asarray(p, float)
+    start = int(np.lexsort((p[:, 1], p[:, 0]))[0])
+    hull, cur = [], start
+    while True:
+        hull.append(cur)
+        nxt = (cur + 1) % len(p)
+        for j in range(len(p)):
+            a, b = p[nxt] - p[cur], p[j] - p[cur]
+            cross = a[0] * b[1] - a[1] * b[0]
+            if cross < 0 or (cross == 0 and np.dot(b, b) > np.dot(a, a)):
+                nxt = j
+        cur = nxt
+        if cur == start:
+            break
+    h = p[hull]
+    return 0.5 * abs(np.dot(h[:, 0], np.roll(h[:, 1], -1)) - np.dot(h[:, 1], np.roll(h[:, 0], -1)))
+
+
+def test_area_of_the_whole_simplex_is_one():
+    assert library.compositional_area(np.array([[100, 0, 0], [0, 100, 0], [0, 0, 100], [30, 30, 40]])) == pytest.approx(1.0)
+    assert library.compositional_area(100 * np.eye(4)) == pytest.approx(1.0)
+
+
+def test_area_of_sub_simplices_closed_form():
+    # the triangle of compositions with every element >= a (at.%) is a simplex scaled by (1 - 3a/100)
+    for a in (5.0, 20.0):
+        pts = np.array([[100 - 2 * a, a, a], [a, 100 - 2 * a, a], [a, a, 100 - 2 * a]])
+        assert library.compositional_area(pts) == pytest.approx((1 - 3 * a / 100) ** 2)
+        pts4 = np.full((4, 4), a) + np.eye(4) * (100 - 4 * a)
+        assert library.compositional_area(pts4) == pytest.approx((1 - 4 * a / 100) ** 3)
+
+
+def test_area_matches_brute_force_hull_on_random_maps():
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        x = rng.dirichlet([4, 3, 2], size=60) * 100
+        # the simplex share is the hull area in the (x1, x2) fractions times 2! = 2
+        want = 2 * _gift_wrap_area(x[:, :2] / 100)
+        assert library.compositional_area(x) == pytest.approx(want, rel=1e-12)
+
+
+def test_diagnose_tilt_recovers_a_known_shrink():
+    """Maps whose spread around the centre shrinks linearly with tilt: the area
+    criterion and the least-squares criterion both return the true tilt."""
+    rng = np.random.default_rng(0)
+    base = rng.dirichlet([5, 5, 5], size=200) * 100 - 100 / 3
+
+    def lib(t):
+        return 100 / 3 + base * (1.0 - 0.02 * (t - 30.0))
+
+    tilts = np.arange(26.0, 34.01, 1.0)
+    d = library.diagnose_tilt(lib(30.6), tilts, [lib(t) for t in tilts])
+    assert d["tilt_area"] == pytest.approx(30.6, abs=0.05)
+    assert d["tilt_lsq"] == pytest.approx(30.6, abs=1e-6)
+    assert all(a > b for a, b in zip(d["areas"], d["areas"][1:]))

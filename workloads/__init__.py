@@ -21,6 +21,7 @@ from .scenes import (
     synthetic_launch_table,
     scene_quaternary,
     scene_tilt_pressure_sweep,
+    scene_tilt_scan,
     scene_large_shielded,
     scene_by_name,
 )
@@ -35,6 +36,7 @@ __all__ = [
     "synthetic_launch_table",
     "scene_quaternary",
     "scene_tilt_pressure_sweep",
+    "scene_tilt_scan",
     "scene_large_shielded",
     "scene_by_name",
 ]

@@ -298,6 +298,33 @@ def scene_tilt_pressure_sweep(n_range=(100_000, 10_000_000), n_pressures=16, n_t
 
 
 # ---------------------------------------------------------------------------
+# Tilt scan: one materials library (a subset of Ni/Pd/Pt/Ru, e.g. the ternary
+# Pd-Pt-Ru library) simulated at several common cathode tilts in one launch.
+# Target centres stay at the 30 deg confocal positions, as in the sweep; the
+# instances are tilt-major (tilt t, element j -> instance t * n_el + j), so the
+# count tallies of one tilt are contiguous; 200x200 int64 counts per instance.
+# ---------------------------------------------------------------------------
+def scene_tilt_scan(tilts, elements=("Pd", "Pt", "Ru"), n_per_cathode=1_000_000, pressure=0.5, T=300.0,
+                    E_i=400.0, nx=200, ny=200, physics=None, seed=0) -> Scene:
+    box_lo, box_hi = (-200.0, -200.0, -100.0), (200.0, 200.0, 200.0)
+    ta30 = math.radians(30.0)
+    radial, zc = 120.0 * math.sin(ta30), 100.0 - 120.0 * math.cos(ta30)
+    prims, geoms, cath, inst = [], [], [], []
+    for ti, t in enumerate(tilts):
+        gprims, poses, sub_local = _quaternary_geometry(float(t), radial=radial, z=zc, box_hi_z=box_hi[2])
+        geoms.append({"prim_begin": len(prims), "prim_count": len(gprims), "substrate": sub_local})
+        for sym in elements:
+            c, nrm, e1, tloc = poses[QUATERNARY.index(sym)]
+            cath.append(_cathode(ELEMENTS[sym], c, nrm, e1, target_local=tloc))
+            inst.append({"geometry": ti, "cathode": len(cath) - 1, "pressure": float(pressure), "E_i": float(E_i),
+                         "k": 0.4, "n": int(n_per_cathode)})
+        prims += gprims
+    grid = default_grid(nx, ny, 50.0, 50.0, count_dtype="int64", energy=False)
+    return Scene("tilt_scan", box_lo, box_hi, GAS_AR, float(T), prims, geoms, cath, inst, grid,
+                 default_physics(**(physics or {})), seed)
+
+
+# ---------------------------------------------------------------------------
 # Large: single Ni cathode, Ar 3 Pa, 1e9 particles, 64 primitives (chimney,
 # substrate group and 57 seeded shields placed off the cathode-substrate line
 # of sight), 512x512 grid + 64-bin energy + 32-bin arrival-angle histograms.
@@ -351,6 +378,7 @@ _BUILDERS = {
     "single_ni_table": scene_single_ni_table,
     "quaternary": scene_quaternary,
     "sweep": scene_tilt_pressure_sweep,
+    "tilt_scan": scene_tilt_scan,
     "large": scene_large_shielded,
 }
 
