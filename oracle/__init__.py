@@ -77,7 +77,9 @@ def lib():
             L.or_scene_new.argtypes = [p, i, p, i, p, i, p, i, p, p, p]
             L.or_scene_free.argtypes = [p]
             L.or_run_ids.restype = i
-            L.or_run_ids.argtypes = [p, u64, C.c_int64, p, p, i, p, p, p, p, p, p, p]
+            L.or_run_ids.argtypes = [p, u64, C.c_int64, p, p, i, p, p, p, p, p, p, p, p]
+            L.or_scene_set_score_T.restype = None
+            L.or_scene_set_score_T.argtypes = [p, i]
             for name, args in {
                 "or_chi": [i, d, d], "or_x0": [i, d, d], "or_chi_hard_sphere": [d],
                 "or_bmax_direct": [i, d, d], "or_bmax_interp": [d, d],
@@ -86,6 +88,7 @@ def lib():
                 "or_c_energy": [], "or_s_gas": [p], "or_n_gas": [p, i], "or_inst_emax": [p, i],
                 "or_cath_ascr": [p, i], "or_sigma": [p, i, d], "or_K": [p, i, d], "or_M": [p, i, d],
                 "or_lambda": [p, i, d], "or_rel_speed_pdf": [d, d, d], "or_integrate_test": [i, d, d],
+                "or_dlnK_dlns": [p, i, d],
             }.items():
                 f = getattr(L, name)
                 f.restype = d
@@ -198,7 +201,9 @@ class OracleScene:
             pass
 
     # -- per-particle transport ------------------------------------------------
-    def run_ids(self, inst_ids, pids, n_threads=None, seed=None):
+    def run_ids(self, inst_ids, pids, n_threads=None, seed=None, score_T=False):
+        """Outcomes of particles (inst_ids[i], pids[i]); score_T adds the
+        temperature score (d ln p(path)/dT at fixed pressure; slower)."""
         inst_ids = np.ascontiguousarray(inst_ids, dtype=np.int32)
         pids = np.ascontiguousarray(pids, dtype=np.uint64)
         n = len(pids)
@@ -207,25 +212,34 @@ class OracleScene:
             "cos": np.empty(n, float), "ncoll": np.empty(n, np.int64), "score": np.empty(n, float),
             "attempts": np.empty(n, np.int64),
         }
+        if score_T:
+            out["score_T"] = np.empty(n, float)
         if n_threads is None:
             n_threads = os.cpu_count() or 1
         seed = self.scene.seed if seed is None else seed
-        rc = lib().or_run_ids(self.h, int(seed), n, _ptr(inst_ids), _ptr(pids), int(n_threads),
-                              _ptr(out["prim"]), _ptr(out["cell"]), _ptr(out["E"]), _ptr(out["cos"]),
-                              _ptr(out["ncoll"]), _ptr(out["score"]), _ptr(out["attempts"]))
+        L = lib()
+        L.or_scene_set_score_T(self.h, 1 if score_T else 0)
+        rc = L.or_run_ids(self.h, int(seed), n, _ptr(inst_ids), _ptr(pids), int(n_threads),
+                          _ptr(out["prim"]), _ptr(out["cell"]), _ptr(out["E"]), _ptr(out["cos"]),
+                          _ptr(out["ncoll"]), _ptr(out["score"]), _ptr(out["attempts"]),
+                          _ptr(out["score_T"]) if score_T else None)
         if rc != 0:
             raise ValueError("or_run_ids rejected its inputs")
         out["inst"] = inst_ids
         out["pid"] = pids
         return out
 
-    def run_all(self, n_threads=None, seed=None):
+    def run_all(self, n_threads=None, seed=None, score_T=False):
         """Every particle of every instance, in ticket order (instance-major)."""
         ids, pids = [], []
         for i, I in enumerate(self.scene.instances):
             ids.append(np.full(int(I["n"]), i, np.int32))
             pids.append(np.arange(int(I["n"]), dtype=np.uint64))
-        return self.run_ids(np.concatenate(ids), np.concatenate(pids), n_threads, seed)
+        return self.run_ids(np.concatenate(ids), np.concatenate(pids), n_threads, seed, score_T)
+
+    def dlnK_dlns(self, cath, v):
+        """d ln K / d ln s at speed v (s = per-axis thermal spread of the gas)."""
+        return lib().or_dlnK_dlns(self.h, int(cath), float(v))
 
     # -- probes -----------------------------------------------------------------
     def sigma(self, cath, g):

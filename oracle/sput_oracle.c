@@ -431,6 +431,7 @@ typedef struct or_scene {
     double half_u, half_v, e_hist_max;
     double chi_min;
     int interaction, gas_motion, max_attempts;
+    int want_score_T; /* compute the temperature score (or_scene_set_score_T) */
     int64_t max_collisions;
     double hs_diameter;
 } or_scene;
@@ -474,23 +475,21 @@ static double rel_speed_pdf(double g, double v, double s)
 typedef struct {
     const or_scene* S;
     const cath_t* c;
-    double v;
+    double v, s;
 } K_ctx;
 
 static double K_integrand(double g, const void* vctx)
 {
     const K_ctx* k = (const K_ctx*)vctx;
-    return sigma_of_g(k->S, k->c, g) * g * rel_speed_pdf(g, k->v, k->S->s_gas);
+    return sigma_of_g(k->S, k->c, g) * g * rel_speed_pdf(g, k->v, k->s);
 }
 
-/* K(v) = <sigma(g) g> over the Maxwellian gas, Angstrom^2 km/s */
-static double K_of_v(const or_scene* S, const cath_t* c, double v)
+/* <sigma(g) g> over a Maxwellian gas of per-axis velocity spread s */
+static double K_of_v_s(const or_scene* S, const cath_t* c, double v, double s)
 {
-    if (S->gas_motion == GAS_STATIONARY) return sigma_of_g(S, c, v) * v;
-    double s = S->s_gas;
     double a = v - 12.0 * s, b = v + 12.0 * s;
     if (a < 0.0) a = 0.0;
-    K_ctx k = {S, c, v};
+    K_ctx k = {S, c, v, s};
     /* split the window into 8 panels around the peak */
     double I = 0.0;
     for (int p = 0; p < 8; ++p) {
@@ -498,6 +497,22 @@ static double K_of_v(const or_scene* S, const cath_t* c, double v)
         I += integrate(K_integrand, &k, x0, x1, 1e-12);
     }
     return I;
+}
+
+/* K(v) = <sigma(g) g> over the Maxwellian gas at T, Angstrom^2 km/s */
+static double K_of_v(const or_scene* S, const cath_t* c, double v)
+{
+    if (S->gas_motion == GAS_STATIONARY) return sigma_of_g(S, c, v) * v;
+    return K_of_v_s(S, c, v, S->s_gas);
+}
+
+/* d ln K / d ln s at fixed v (s = sqrt(kT/m_gas), so d ln K / dT = this / (2T)):
+ * central difference of the quadrature; 0 for a gas at rest */
+static double dlnK_dlns(const or_scene* S, const cath_t* c, double v)
+{
+    if (S->gas_motion == GAS_STATIONARY) return 0.0;
+    const double h = 1e-4, s = S->s_gas;
+    return (K_of_v_s(S, c, v, s * (1.0 + h)) - K_of_v_s(S, c, v, s * (1.0 - h))) / (2.0 * h * K_of_v_s(S, c, v, s));
 }
 
 /* mean free path lambda_m(v) = v / (n_g K(v)), mm */
@@ -812,6 +827,7 @@ typedef struct {
     double cosang; /* |cos| of arrival angle to the substrate normal (front hits) */
     int64_t ncoll;
     double score;  /* d ln p(path) / d ln n_gas */
+    double score_T; /* d ln p(path) / dT at fixed pressure, 1/K (when requested) */
     int64_t attempts;
 } outcome_t;
 
@@ -859,7 +875,8 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
     }
     double speed = speed_of_E(E, c->mass);
     int64_t ncoll = 0, attempts = 0;
-    double score = 0.0;
+    double score = 0.0, score_T = 0.0;
+    o->score_T = 0.0;
     trace_row(tr, rows, 0, p, d, speed, -1, 0.0, 0.0);
 
     for (uint32_t k = 1;; ++k) {
@@ -869,8 +886,13 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         double ell = I->n_gas > 0.0 ? -lam * log(rn(w[0])) : INFINITY;
         double t;
         int hit = hit_test(S, G, p, d, ell, k == 1 ? c->target : -1, &t);
+        /* temperature score: the collision rate n_g K(v)/v with n_g = p/(k_B T)
+         * has d ln(rate)/dT = (-1 + G/2)/T, G = d ln K/d ln s */
+        double Gv = S->want_score_T ? dlnK_dlns(S, c, speed) : 0.0;
+        double aT = (-1.0 + 0.5 * Gv) / S->T;
         if (hit >= 0) {
             score -= t / lam;
+            score_T -= aT * t / lam;
             double q[3] = {p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2]};
             trace_row(tr, rows, (int)k, q, d, speed, 1, hit, t);
             o->prim = hit;
@@ -896,11 +918,13 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
             }
             o->ncoll = ncoll;
             o->score = score;
+            o->score_T = score_T;
             o->attempts = attempts;
             return;
         }
         for (int a = 0; a < 3; ++a) p[a] += ell * d[a];
         score += 1.0 - ell / lam;
+        score_T += aT * (1.0 - ell / lam);
         if ((int64_t)k > S->max_collisions) {
             trace_row(tr, rows, (int)k, p, d, speed, 2, 0.0, ell);
             o->prim = -1;
@@ -909,6 +933,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
             o->cosang = 0.0;
             o->ncoll = ncoll;
             o->score = score;
+            o->score_T = score_T;
             o->attempts = attempts;
             return;
         }
@@ -916,6 +941,9 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         double V[3], vo[3], Vo[3];
         int na = sample_partner(S, c, &st, k, v, V);
         attempts += na;
+        /* partner density f_T(V) sigma(g) g / K(v): d ln/dT = -3/(2T) + |V|^2/(2 s^2 T) - G/(2T) */
+        if (S->want_score_T && S->gas_motion == GAS_THERMAL)
+            score_T += (-1.5 + 0.5 * dot3(V, V) / (S->s_gas * S->s_gas) - 0.5 * Gv) / S->T;
         collide_with(S, c, v, V, rn(w[1]), rn(w[2]), vo, Vo, NULL);
         speed = sqrt(dot3(vo, vo));
         for (int a = 0; a < 3; ++a) d[a] = vo[a] / speed;
@@ -1060,6 +1088,7 @@ typedef struct {
     int32_t *prim, *cell;
     double *E, *cosang, *score;
     int64_t *ncoll, *attempts;
+    double* score_T;
 } run_job;
 
 static void* run_worker(void* arg)
@@ -1075,6 +1104,7 @@ static void* run_worker(void* arg)
         j->ncoll[i] = o.ncoll;
         j->score[i] = o.score;
         j->attempts[i] = o.attempts;
+        if (j->score_T) j->score_T[i] = o.score_T;
     }
     return NULL;
 }
@@ -1082,7 +1112,7 @@ static void* run_worker(void* arg)
 /* transport the particles (inst[i], pid[i]) for i < n with n_threads threads */
 int or_run_ids(const or_scene* S, uint64_t seed, int64_t n, const int32_t* inst, const uint64_t* pid, int n_threads,
                int32_t* prim, int32_t* cell, double* E, double* cosang, int64_t* ncoll, double* score,
-               int64_t* attempts)
+               int64_t* attempts, double* score_T)
 {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
@@ -1095,7 +1125,7 @@ int or_run_ids(const or_scene* S, uint64_t seed, int64_t n, const int32_t* inst,
     for (int t = 0; t < n_threads; ++t) {
         int64_t b = t * per, e = (t + 1) * per < n ? (t + 1) * per : n;
         if (b >= e) break;
-        run_job J = {S, seed, inst, pid, b, e, prim, cell, E, cosang, score, ncoll, attempts};
+        run_job J = {S, seed, inst, pid, b, e, prim, cell, E, cosang, score, ncoll, attempts, score_T};
         jobs[t] = J;
         pthread_create(&th[t], NULL, run_worker, &jobs[t]);
         ++used;
@@ -1106,6 +1136,9 @@ int or_run_ids(const or_scene* S, uint64_t seed, int64_t n, const int32_t* inst,
 
 /* ------------------------------------------------ probes for unit tests */
 int or_version(void) { return OR_VERSION; }
+/* compute the temperature score in or_run_ids from now on (slower: three quadratures per flight) */
+void or_scene_set_score_T(or_scene* S, int on) { S->want_score_T = on; }
+double or_dlnK_dlns(const or_scene* S, int cath, double v) { return dlnK_dlns(S, &S->cath[cath], v); }
 double or_c_energy(void) { return c_energy(); }
 double or_s_gas(const or_scene* S) { return S->s_gas; }
 double or_n_gas(const or_scene* S, int inst) { return S->inst[inst].n_gas; }
