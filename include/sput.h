@@ -64,7 +64,7 @@
 extern "C" {
 #endif
 
-#define SPUT_ABI_VERSION 2
+#define SPUT_ABI_VERSION 3
 
 typedef enum sput_status {
     SPUT_OK = 0,
@@ -214,6 +214,9 @@ typedef struct sput_tallies {
     int64_t* hist_E;
     int64_t* hist_A;
     sput_record* records;
+    double* score_T;             /* [inst][ny][nx] sum over landings of d ln p(path)/dT at fixed
+                                    pressure (1/K): the collision rate through n_g = p/(k_B T) and
+                                    <sigma g>(v; T), and the Maxwellian partner density */
 } sput_tallies;
 
 typedef struct sput_tally_layout {

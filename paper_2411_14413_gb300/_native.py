@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # --------------------------------------------------------------- ABI mirror
-SPUT_ABI_VERSION = 2
+SPUT_ABI_VERSION = 3
 SPUT_OK = 0
 STATUS_NAMES = {0: "SPUT_OK", 1: "SPUT_ERR_INVALID_ARG", 2: "SPUT_ERR_INVALID_SCENE", 3: "SPUT_ERR_CUDA",
                 4: "SPUT_ERR_TIMEOUT", 5: "SPUT_ERR_DEVICE_CHECK", 6: "SPUT_ERR_UNSUPPORTED", 7: "SPUT_ERR_NO_MEMORY"}
@@ -141,7 +141,7 @@ class sput_record(C.Structure):
 class sput_tallies(C.Structure):
     _fields_ = [("counts", C.c_void_p), ("energy", C.c_void_p), ("score", C.c_void_p),
                 ("prim_counts", C.c_void_p), ("timed_out", C.c_void_p), ("hist_E", C.c_void_p),
-                ("hist_A", C.c_void_p), ("records", C.c_void_p)]
+                ("hist_A", C.c_void_p), ("records", C.c_void_p), ("score_T", C.c_void_p)]
 
 
 class sput_tally_layout(C.Structure):

@@ -200,7 +200,7 @@ class Transport:
     ``run()`` transports every particle (or a ticket range) and returns the
     device tallies; nothing is computed in Python."""
 
-    def __init__(self, scene, device=0, energy=None, score=False, records=False, prim_counts=True,
+    def __init__(self, scene, device=0, energy=None, score=False, records=False, prim_counts=True, score_T=False,
                  histograms=None):
         import torch
 
@@ -217,6 +217,8 @@ class Transport:
             self.t["energy"] = torch.zeros((ni, L.ny, L.nx), dtype=torch.float64, device=dev)
         if score:
             self.t["score"] = torch.zeros((ni, L.ny, L.nx), dtype=torch.float64, device=dev)
+        if score_T:
+            self.t["score_T"] = torch.zeros((ni, L.ny, L.nx), dtype=torch.float64, device=dev)
         if prim_counts:
             self.t["prim_counts"] = torch.zeros((ni, L.max_prims), dtype=torch.int64, device=dev)
             self.t["timed_out"] = torch.zeros((ni,), dtype=torch.int64, device=dev)

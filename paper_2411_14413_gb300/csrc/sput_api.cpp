@@ -389,9 +389,9 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     for (size_t p = 0; p < S->pair_phys.size(); ++p) {
         const PairPhys& pp = S->pair_phys[p];
         double v_top = std::sqrt(2.0 * S->pair_E_top[p] / (pp.m1 * kEnergyUnit)) + 12.0 * S->s_gas;
-        std::vector<float4> K, M;
+        std::vector<float4> K, M, Gt;
         int n_w = 0;
-        build_w_tables(pp, S->bt, S->s_gas, thermal, v_top, h_w, K, M, n_w);
+        build_w_tables(pp, S->bt, S->s_gas, thermal, v_top, h_w, K, M, Gt, n_w);
         DevPair& D = S->dpairs[p];
         D.kappa = (float)pp.kappa;
         D.ln_kappa = (float)std::log(pp.kappa);
@@ -403,6 +403,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         S->wtab.insert(S->wtab.end(), K.begin(), K.end());
         D.M_off = (int)S->wtab.size();
         S->wtab.insert(S->wtab.end(), M.begin(), M.end());
+        D.G_off = (int)S->wtab.size();
+        S->wtab.insert(S->wtab.end(), Gt.begin(), Gt.end());
         D.n_w = n_w;
         D.w_inv_h = (float)(1.0 / h_w);
         D.inv_s = (float)(1.0 / S->s_gas);
@@ -572,6 +574,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         p.box_hi[a] = (float)S->chamber.box_hi[a];
     }
     p.s_gas = (float)S->s_gas;
+    p.inv_T = (float)(1.0 / S->chamber.gas_T);
+    p.inv_s2 = (float)(1.0 / (S->s_gas * S->s_gas));
     p.gas_thermal = thermal;
     p.max_attempts = S->physics.max_attempts;
     p.max_prims = S->max_prims;
@@ -659,7 +663,7 @@ sput_status sput_tally_layout_get(const sput_scene* S, sput_tally_layout* out)
 namespace {
 
 struct TallySizes {
-    size_t counts, energy, score, prim_counts, timed_out, hist_E, hist_A;
+    size_t counts, energy, score, prim_counts, timed_out, hist_E, hist_A, score_T;
 };
 
 TallySizes tally_sizes(const sput_scene* S)
@@ -673,6 +677,7 @@ TallySizes tally_sizes(const sput_scene* S)
     t.timed_out = ni * 8;
     t.hist_E = ni * S->grid.n_ebins * 8;
     t.hist_A = ni * S->grid.n_abins * 8;
+    t.score_T = ni * nc * 8;
     return t;
 }
 
@@ -704,6 +709,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     p.counts = T->counts;
     p.energy = T->energy;
     p.score = T->score;
+    p.score_T = T->score_T;
     p.prim_counts = reinterpret_cast<long long*>(T->prim_counts);
     p.timed_out = reinterpret_cast<long long*>(T->timed_out);
     p.hist_E = reinterpret_cast<long long*>(T->hist_E);
@@ -728,6 +734,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
         if (T->timed_out) CUDA_TRY(cudaMemsetAsync(T->timed_out, 0, sz.timed_out, stream));
         if (T->hist_E) CUDA_TRY(cudaMemsetAsync(T->hist_E, 0, sz.hist_E, stream));
         if (T->hist_A) CUDA_TRY(cudaMemsetAsync(T->hist_A, 0, sz.hist_A, stream));
+        if (T->score_T) CUDA_TRY(cudaMemsetAsync(T->score_T, 0, sz.score_T, stream));
     }
     CUDA_TRY(cudaMemsetAsync(scratch, 0, 64, stream));
 
@@ -809,9 +816,10 @@ sput_status sput_run_host(sput_scene* S, const sput_run_opts* opts, const sput_t
     sput_status st = ensure_scratch(S);
     if (st != SPUT_OK) return st;
     const TallySizes sz = tally_sizes(S);
-    size_t off[7], o = 0;
-    const size_t bytes[7] = {sz.counts, sz.energy, sz.score, sz.prim_counts, sz.timed_out, sz.hist_E, sz.hist_A};
-    for (int i = 0; i < 7; ++i) {
+    size_t off[8], o = 0;
+    const size_t bytes[8] = {sz.counts, sz.energy, sz.score, sz.prim_counts, sz.timed_out, sz.hist_E, sz.hist_A,
+                             sz.score_T};
+    for (int i = 0; i < 8; ++i) {
         off[i] = o;
         o = align_up(o + bytes[i], 256);
     }
@@ -825,22 +833,23 @@ sput_status sput_run_host(sput_scene* S, const sput_run_opts* opts, const sput_t
     }
     if (!S->own_stream) CUDA_TRY(cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking));
     unsigned char* base = reinterpret_cast<unsigned char*>(S->d_stage);
-    void* hp[7] = {H->counts, H->energy, H->score, H->prim_counts, H->timed_out, H->hist_E, H->hist_A};
+    void* hp[8] = {H->counts, H->energy, H->score, H->prim_counts, H->timed_out, H->hist_E, H->hist_A, H->score_T};
     sput_tallies D{};
-    void** dp[7] = {&D.counts, reinterpret_cast<void**>(&D.energy), reinterpret_cast<void**>(&D.score),
+    void** dp[8] = {&D.counts, reinterpret_cast<void**>(&D.energy), reinterpret_cast<void**>(&D.score),
                     reinterpret_cast<void**>(&D.prim_counts), reinterpret_cast<void**>(&D.timed_out),
-                    reinterpret_cast<void**>(&D.hist_E), reinterpret_cast<void**>(&D.hist_A)};
-    for (int i = 0; i < 7; ++i) *dp[i] = hp[i] ? base + off[i] : nullptr;
+                    reinterpret_cast<void**>(&D.hist_E), reinterpret_cast<void**>(&D.hist_A),
+                    reinterpret_cast<void**>(&D.score_T)};
+    for (int i = 0; i < 8; ++i) *dp[i] = hp[i] ? base + off[i] : nullptr;
     sput_run_opts o2 = *opts;
     if (o2.accumulate) {
         // accumulate into the caller's host values: upload them first
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 8; ++i)
             if (hp[i]) CUDA_TRY(cudaMemcpyAsync(base + off[i], hp[i], bytes[i], cudaMemcpyHostToDevice, S->own_stream));
     }
     sput_run_stats local{};
     st = run_impl(S, &o2, S->own_stream, &D, stats ? stats : &local, S->d_scratch);
     if (st != SPUT_OK) return st;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 8; ++i)
         if (hp[i]) CUDA_TRY(cudaMemcpyAsync(hp[i], base + off[i], bytes[i], cudaMemcpyDeviceToHost, S->own_stream));
     CUDA_TRY(cudaStreamSynchronize(S->own_stream));
     return SPUT_OK;

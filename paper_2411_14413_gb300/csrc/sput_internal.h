@@ -87,7 +87,7 @@ struct alignas(16) DevPair {
     int n_w;            // intervals of the w tables
     float w_inv_h;      // 1 / Delta w
     float inv_s;        // 1 / s_gas, w = ln(1 + v / s_gas)
-    float pad;
+    int G_off;          // float4 offset of the d ln K / d ln s table (zero for a gas at rest)
 };
 
 struct alignas(16) DevInstance {
@@ -120,6 +120,7 @@ struct Params {
     float bm_lo, bm_inv_h;
     float box_lo[3], box_hi[3];
     float s_gas;
+    float inv_T, inv_s2;               // 1/T (1/K), 1/s_gas^2
     int gas_thermal;
     int max_attempts;
     int max_prims;
@@ -134,6 +135,7 @@ struct Params {
     void* counts;
     double* energy;
     double* score;
+    double* score_T;                   // temperature score tally (null = off)
     long long* prim_counts;
     long long* timed_out;
     long long* hist_E;
@@ -160,6 +162,7 @@ constexpr int kTraceRows = 64;
 // Launchers implemented in sput_transport.cu.
 int transport_configure(int max_dynamic_smem);
 int transport_launch(const Params& p, int count64, int blocks, int threads, size_t smem, void* stream);
+// (the launch picks the kernel instance with the temperature score when p.score_T is set)
 size_t transport_smem_bytes(const Params& p);
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem);
 int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev, double* y_dev, void* stream);

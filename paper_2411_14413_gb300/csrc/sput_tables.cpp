@@ -303,12 +303,12 @@ double M64(const PairPhys& pp, const BmaxTable* bt, double s, double v, int mono
 }
 
 void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s, int thermal, double v_top, double h_w,
-                    std::vector<float4>& K, std::vector<float4>& M, int& n_w)
+                    std::vector<float4>& K, std::vector<float4>& M, std::vector<float4>& G, int& n_w)
 {
     double w_top = std::log1p(v_top / s);
     n_w = std::max(4, (int)std::ceil(w_top / h_w));
     int mono = h_monotone(pp, bt, v_top + 20.0 * s);
-    std::vector<double> kv(3 * n_w + 1), mv(3 * n_w + 1);
+    std::vector<double> kv(3 * n_w + 1), mv(3 * n_w + 1), gv(3 * n_w + 1);
     unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     std::vector<std::thread> th;
     for (unsigned t = 0; t < nt; ++t)
@@ -319,14 +319,21 @@ void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s, int therm
                 // path n sigma(v) stays finite when the speed decays towards zero
                 kv[j] = thermal ? K64(pp, bt, s, 1, v) : sigma64(pp, bt, v);
                 mv[j] = thermal ? M64(pp, bt, s, v, mono) : 0.0;
+                // d ln K / d ln s at fixed v by a central difference in s (gas at rest: 0)
+                const double hs = 1e-4;
+                gv[j] = thermal ? (K64(pp, bt, s * (1.0 + hs), 1, v) - K64(pp, bt, s * (1.0 - hs), 1, v)) /
+                                      (2.0 * hs * kv[j])
+                                : 0.0;
             }
         });
     for (auto& x : th) x.join();
     K.resize(n_w);
     M.resize(n_w);
+    G.resize(n_w);
     for (int i = 0; i < n_w; ++i) {
         K[i] = cubic_from_thirds(kv[3 * i], kv[3 * i + 1], kv[3 * i + 2], kv[3 * i + 3]);
         M[i] = cubic_from_thirds(mv[3 * i], mv[3 * i + 1], mv[3 * i + 2], mv[3 * i + 3]);
+        G[i] = cubic_from_thirds(gv[3 * i], gv[3 * i + 1], gv[3 * i + 2], gv[3 * i + 3]);
     }
 }
 

@@ -60,7 +60,7 @@ double sigma64(const PairPhys& pp, const BmaxTable* bt, double g);
 // K(v) = <sigma(g) g> over the Maxwellian gas (gas at rest: sigma(v) = K(v)/v) and the
 // rejection bound M(v) = max_{g <= v + 6 s} sigma(g) g.
 void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v_top,
-                    double h_w, std::vector<float4>& K, std::vector<float4>& M, int& n_w);
+                    double h_w, std::vector<float4>& K, std::vector<float4>& M, std::vector<float4>& G, int& n_w);
 
 // FP64 host values used by tests through the probe entry point.
 double K64(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v);

@@ -191,6 +191,7 @@ __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& b1, fl
 // ------------------------------------------------------------- launch
 struct Lane {
     float px, py, pz, dx, dy, dz, speed, score;
+    float scoreT;  // d ln p(path)/dT (kernel instance with the temperature score only)
     uint32_t pid, inst, k, ncoll;
     int gbegin, gcount, gsub, target, pair;
     float ng14, E_per_v2;
@@ -248,6 +249,18 @@ __device__ int table_pick(const float* F, int n, float u, float& t)
     return lo;
 }
 
+// Joint table draw (kept out of line: rare, and off the registers of the hot loop):
+// mu from the marginal CDF F (u_mu), E from the conditional CDF of the drawn mu cell (u_E).
+__device__ __noinline__ void table_launch(const float* F, int nmu, int nE, float dE, float u_mu, float u_E, float& mu,
+                                          float& E)
+{
+    float tm, te;
+    const int i = table_pick(F, nmu, u_mu, tm);
+    const int k = table_pick(F + (nmu + 1) + i * (nE + 1), nE, u_E, te);
+    mu = ((float)i + tm) / (float)nmu;
+    E = ((float)k + te) * dE;
+}
+
 __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t inst, uint32_t pid, float& px,
                              float& py, float& pz, float& dx, float& dy, float& dz, float& E)
 {
@@ -260,13 +273,7 @@ __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t ins
     sincospif(2.0f * rn(w0.y), &sa, &ca);
     float mu;
     if (C.lt_off >= 0) {
-        // joint table: mu from the marginal (word 3), E from the drawn row (word 2)
-        const float* F = P.lt_tab + C.lt_off;
-        float tm, te;
-        const int i = table_pick(F, C.lt_nmu, rn(w0.w), tm);
-        const int k = table_pick(F + (C.lt_nmu + 1) + i * (C.lt_nE + 1), C.lt_nE, rn(w0.z), te);
-        mu = ((float)i + tm) / (float)C.lt_nmu;
-        E = ((float)k + te) * C.lt_dE;
+        table_launch(P.lt_tab + C.lt_off, C.lt_nmu, C.lt_nE, C.lt_dE, rn(w0.w), rn(w0.z), mu, E);
     } else {
         const float s = sqrtf(rn(w0.z)) * I.thompson_q;
         E = I.U_s * s / (1.0f - s);
@@ -357,6 +364,7 @@ __device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, u
     S.k = 0u;
     S.ncoll = 0u;
     S.score = 0.0f;
+    S.scoreT = 0.0f;
 }
 
 // ------------------------------------------------------------- one flight
@@ -367,12 +375,14 @@ struct StepOut {
     int prim;       // landing: local primitive index
     int attempts;   // partner attempts of this collision
     int nonfinite;  // the state became NaN/Inf
+    float Gv;       // d ln K / d ln s at the flight's speed (temperature score only)
 };
 
 // Free flight k+1 of the atom in S and the surface test.  Landing: S keeps the
 // pre-flight position and out.t is the hit distance.  Otherwise the atom moves
 // to the collision point; w is the flight's Philox block (words 1 and 2, the
 // impact parameter and azimuth, are used by the collision; word 3 is unused).
+template <bool kScoreT>
 __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
                            StepOut& out, uint4& w)
 {
@@ -386,6 +396,12 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
     const float inv_lam = P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv;
     const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
+    // temperature score: d ln(n_g K(v)/v)/dT = (-1 + G/2)/T with n_g = p/(k_B T), G = d ln K/d ln s
+    float aT = 0.0f;
+    if (kScoreT) {
+        out.Gv = wtab_eval(T, pr, pr.G_off, S.speed);
+        aT = (0.5f * out.Gv - 1.0f) * P.inv_T;
+    }
 
     // surface test: nearest hit, ties to the lowest index; the emitting target
     // is skipped on the first flight
@@ -410,6 +426,7 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     }
     if (hb >= 0 && tb <= ell) {
         S.score -= tb * inv_lam;
+        if (kScoreT) S.scoreT -= aT * tb * inv_lam;
         out.t = tb;
         out.prim = hb;
         return kStepLanded;
@@ -419,6 +436,7 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     S.py = fmaf(ell, S.dy, S.py);
     S.pz = fmaf(ell, S.dz, S.pz);
     S.score += 1.0f - ell * inv_lam;
+    if (kScoreT) S.scoreT += aT * (1.0f - ell * inv_lam);
     if (!isfinite(S.px + S.py + S.pz + S.speed)) {
         out.nonfinite = 1;
         return kStepTimedOut;
@@ -579,13 +597,15 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
 // One flight of every active lane of the warp (flight, surface test, then for
 // the lanes that collide: warp-wide partner sampling and the scattering).
 // Must be called by all 32 lanes together; inactive lanes return kStepNone.
+template <bool kScoreT>
 __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const TableView& T, const DevPrim* prims,
                                 const DevPair* pairs, StepOut& out)
 {
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
     int res = kStepNone;
     out.attempts = 0;
-    if (active) res = flight_move(S, P, T, prims, pairs, out, w);
+    if (kScoreT) out.Gv = 0.0f;
+    if (active) res = flight_move<kScoreT>(S, P, T, prims, pairs, out, w);
     const bool coll = res == kStepCollided;
     const DevPair pr = pairs[S.pair];
     const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
@@ -594,6 +614,9 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
         const float M = coll ? wtab_eval(T, pr, pr.M_off, S.speed) : 0.0f;
         partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, M, Vx, Vy, Vz,
                             out.attempts);
+        // partner density f_T(V) sigma(g) g / K(v): d ln/dT = (|V|^2/(2 s^2) - 3/2 - G/2)/T
+        if (kScoreT && coll)
+            S.scoreT += (0.5f * (Vx * Vx + Vy * Vy + Vz * Vz) * P.inv_s2 - 1.5f - 0.5f * out.Gv) * P.inv_T;
     }
     if (coll) scatter(S, P, T, pr, vx, vy, vz, Vx, Vy, Vz, w);
     return res;
@@ -642,7 +665,7 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
     for (size_t i = (bytes / 16) * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
 }
 
-template <bool kCount64>
+template <bool kCount64, bool kScoreT>
 __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -685,7 +708,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     const int ncell = P.nx * P.ny;
 
     Lane S;
-    S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = 0.0f;
+    S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = S.scoreT = 0.0f;
     S.pid = S.inst = S.k = S.ncoll = 0u;
     S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
     S.ng14 = S.E_per_v2 = 0.0f;
@@ -739,7 +762,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
 
         // ---------------------------------------------------- one flight (all lanes together)
         StepOut so;
-        const int res = flight_step_warp(alive, S, P, T, s_prims, s_pairs, so);
+        const int res = flight_step_warp<kScoreT>(alive, S, P, T, s_prims, s_pairs, so);
         if (alive) ++c_flights;
         c_att += so.attempts;
         if (res == kStepLanded) {
@@ -774,6 +797,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
                 }
                 if (P.energy) atomicAdd(P.energy + ci, (double)E);
                 if (P.score) atomicAdd(P.score + ci, (double)S.score);
+                if (kScoreT) atomicAdd(P.score_T + ci, (double)S.scoreT);
                 if (P.hist_E) {
                     int b = min(max((int)(E * P.ebin_per_eV), 0), P.n_ebins - 1);
                     atomicAdd(reinterpret_cast<unsigned long long*>(P.hist_E) + (size_t)S.inst * P.n_ebins + b, 1ull);
@@ -869,7 +893,7 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         // the flight step is warp-collective, so lanes past n take part without a particle
         const bool valid = i < n;
         Lane S;
-        S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = 0.0f;
+        S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = S.scoreT = 0.0f;
         S.pid = S.inst = S.k = S.ncoll = 0u;
         S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
         S.ng14 = S.E_per_v2 = 0.0f;
@@ -886,7 +910,7 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         for (int r = 1; r < kTraceRows; ++r) {
             if (!__any_sync(kFull, running)) break;
             StepOut so;
-            const int status = flight_step_warp(running, S, P, T, P.prims, P.pairs, so);
+            const int status = flight_step_warp<false>(running, S, P, T, P.prims, P.pairs, so);
             if (running) {
                 double* q = o + (size_t)r * 10;
                 float px = S.px, py = S.py, pz = S.pz;
@@ -935,26 +959,39 @@ size_t transport_smem_bytes(const Params& p) { return smem_layout(p).total; }
 
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem)
 {
-    int nb = 0;
-    cudaError_t e;
-    if (count64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<true>, threads, smem);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<false>, threads, smem);
-    return e == cudaSuccess ? nb : 0;
+    // the smaller occupancy of the instances with and without the temperature score
+    int nb = 0, nt = 0;
+    cudaError_t e, e2;
+    if (count64) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<true, false>, threads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, transport_kernel<true, true>, threads, smem);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<false, false>, threads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, transport_kernel<false, true>, threads, smem);
+    }
+    return (e == cudaSuccess && e2 == cudaSuccess) ? (nb < nt ? nb : nt) : 0;
 }
 
 int transport_configure(int max_dynamic_smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(transport_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(transport_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(transport_kernel<true, false>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, false>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<true, true>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, true>, a, max_dynamic_smem);
     return (int)e;
 }
 
 int transport_launch(const Params& p, int count64, int blocks, int threads, size_t smem, void* stream)
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (count64) transport_kernel<true><<<blocks, threads, smem, s>>>(p);
-    else transport_kernel<false><<<blocks, threads, smem, s>>>(p);
+    if (p.score_T) {
+        if (count64) transport_kernel<true, true><<<blocks, threads, smem, s>>>(p);
+        else transport_kernel<false, true><<<blocks, threads, smem, s>>>(p);
+    } else {
+        if (count64) transport_kernel<true, false><<<blocks, threads, smem, s>>>(p);
+        else transport_kernel<false, false><<<blocks, threads, smem, s>>>(p);
+    }
     return (int)cudaGetLastError();
 }
 
