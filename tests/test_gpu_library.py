@@ -34,25 +34,27 @@ def test_tilt_scan_maps_and_diagnosis(pkg, oracle_mod):
 
     cal, power = _calibration(), np.array([30.0, 12.0, 18.0])
     patch, pts, ref = measurement_patches()
-    true_tilt, n = 30.6, 4_000_000
+    # 1e8 atoms per cathode, as in the paper: the count noise of the reference
+    # patch moves a whole map, so fewer atoms blur the tilt estimate
+    true_tilt, n = 30.6, 100_000_000
     meas_sc = workloads.scene_tilt_scan([true_tilt], elements=EL, n_per_cathode=n, seed=123)
     tr = pkg.Transport(meas_sc, energy=False, prim_counts=False)
     meas = library.composition_maps(tr, 3, patch, ref, cal, power, seed=123)[0].cpu().numpy()
     tr.close()
-    tilts = np.arange(26.0, 34.01, 1.0)
+    tilts = np.arange(27.0, 34.01, 1.0)
     sc = workloads.scene_tilt_scan(tilts, elements=EL, n_per_cathode=n)
     tr = pkg.Transport(sc, energy=False, prim_counts=False)
     sims = library.composition_maps(tr, 3, patch, ref, cal, power, seed=0).cpu().numpy()
     counts = tr.t["counts"].cpu().numpy().reshape(len(tilts), 3, -1).astype(np.float64)
     tr.close()
     rates = np.array([oracle_mod.rate_line(calibration_points(s), P)[0] for s, P in zip(EL, power)])
-    for t in (0, 4, 8):
+    for t in (0, 4, 7):
         want, _ = oracle_mod.composition(counts[t], patch, ref, rates, cal[:, 4], cal[:, 5])
         assert np.allclose(sims[t], want, rtol=1e-12, atol=1e-10)
     d = library.diagnose_tilt(meas, tilts, sims)
     print("tilt diagnosis:", {k: d[k] for k in ("tilt_area", "tilt_lsq", "area_measured")},
-          "areas", np.round(d["areas"], 5))
+          "areas", np.round(d["areas"], 5), "mse", np.round(d["mse"], 4))
     # a larger common tilt shrinks the covered compositional area
     assert d["areas"][0] > d["areas"][-1]
-    assert abs(d["tilt_lsq"] - true_tilt) < 0.5, d
-    assert d["tilt_area"] is not None and abs(d["tilt_area"] - true_tilt) < 1.5, d
+    assert d["tilt_area"] is not None and abs(d["tilt_area"] - true_tilt) < 0.75, d
+    assert abs(d["tilt_lsq"] - true_tilt) < 1.0, d
