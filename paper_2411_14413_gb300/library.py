@@ -102,7 +102,10 @@ def diagnose_tilt(measured, tilts, simulated):
     simulated compositional area equals the measured one (linear interpolation
     between the bracketing tilts; None when no bracket exists), the tilt of
     least mean squared composition difference (parabola through the best
-    three), and the per-tilt areas and mean squared differences."""
+    three), and the per-tilt areas and mean squared differences.  The area
+    criterion is the one the paper uses; the point-by-point least squares is
+    sensitive to the count noise of the reference patch, which moves a whole
+    map, and needs far more atoms for the same precision."""
     tilts = np.asarray(tilts, dtype=np.float64)
     sim = np.asarray(simulated, dtype=np.float64)
     meas = np.asarray(measured, dtype=np.float64)
