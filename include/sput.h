@@ -240,6 +240,10 @@ typedef struct sput_run_opts {
 /* sput_run_opts.flags */
 #define SPUT_RUN_NO_SMEM_COUNTERS 1 /* count landings per primitive with global atomics only */
 #define SPUT_RUN_SMEM_COUNTERS 2    /* privatise them in shared memory (when they fit); default: scene choice */
+#define SPUT_RUN_LAUNCH_AT_CUTOFF 4 /* every atom launches with E = E_max (all other draws unchanged): the
+                                       boundary run of the derivative with respect to the Thompson cut-off,
+                                       d E[f]/dE_max = p(E_max) (E[f | E = E_max] - E[f]),
+                                       p(E_max) = 2 U_s / (E_max (E_max + U_s)); Thompson cathodes only */
 
 typedef struct sput_run_stats {
     uint64_t particles;          /* particles that completed (landed or timed out) */
@@ -377,6 +381,19 @@ sput_status sput_backward(const sput_scene* scene, const double* grad_counts, co
 sput_status sput_composition(int n_cathodes, int n_cells, int n_points, const int64_t* counts,
                              const int32_t* patch_of_cell, int ref_point, const double* calibration,
                              const double* power, double* patch_counts, double* composition, void* stream);
+
+/* Derivative with respect to the incident ion energy E_i of every instance, through the
+ * Thompson cut-off E_max = k Lambda E_i - U_s (Eq. for phi(E)); E_i follows the discharge
+ * voltage, hence the cathode power.  The launch density moves its support with E_max, so
+ *   d E[count_c]/dE_max = p(E_max) (E[count_c | E = E_max] - E[count_c]),
+ *   p(E_max) = 2 U_s / (E_max (E_max + U_s)),
+ * and grad_ion_energy[i] = k Lambda p(E_max) sum_c grad_counts[i][c] (counts_cutoff[i][c] - counts[i][c]).
+ * counts: a run's count tally; counts_cutoff: the same particles and seed run with
+ * SPUT_RUN_LAUNCH_AT_CUTOFF (DEVICE, the scene's count type, [inst][ny][nx]); grad_counts
+ * DEVICE double [inst][ny][nx]; grad_ion_energy DEVICE double [inst], per eV.  Thompson
+ * cathodes only (a launch table has no cut-off).  Asynchronous on `stream`. */
+sput_status sput_emax_backward(const sput_scene* scene, const double* grad_counts, const void* counts,
+                               const void* counts_cutoff, double* grad_ion_energy, void* stream);
 
 /* Backward pass of sput_composition: from grad_composition (DEVICE [n_points][n_cathodes])
  * and the forward's patch_counts, writes grad_patch (DEVICE [n_cathodes][n_points], scratch

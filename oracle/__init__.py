@@ -80,6 +80,8 @@ def lib():
             L.or_run_ids.argtypes = [p, u64, C.c_int64, p, p, i, p, p, p, p, p, p, p, p]
             L.or_scene_set_score_T.restype = None
             L.or_scene_set_score_T.argtypes = [p, i]
+            L.or_scene_set_at_cutoff.restype = None
+            L.or_scene_set_at_cutoff.argtypes = [p, i]
             for name, args in {
                 "or_chi": [i, d, d], "or_x0": [i, d, d], "or_chi_hard_sphere": [d],
                 "or_bmax_direct": [i, d, d], "or_bmax_interp": [d, d],
@@ -201,9 +203,10 @@ class OracleScene:
             pass
 
     # -- per-particle transport ------------------------------------------------
-    def run_ids(self, inst_ids, pids, n_threads=None, seed=None, score_T=False):
+    def run_ids(self, inst_ids, pids, n_threads=None, seed=None, score_T=False, at_cutoff=False):
         """Outcomes of particles (inst_ids[i], pids[i]); score_T adds the
-        temperature score (d ln p(path)/dT at fixed pressure; slower)."""
+        temperature score (d ln p(path)/dT at fixed pressure; slower);
+        at_cutoff launches every atom with E = E_max (boundary run)."""
         inst_ids = np.ascontiguousarray(inst_ids, dtype=np.int32)
         pids = np.ascontiguousarray(pids, dtype=np.uint64)
         n = len(pids)
@@ -219,6 +222,7 @@ class OracleScene:
         seed = self.scene.seed if seed is None else seed
         L = lib()
         L.or_scene_set_score_T(self.h, 1 if score_T else 0)
+        L.or_scene_set_at_cutoff(self.h, 1 if at_cutoff else 0)
         rc = L.or_run_ids(self.h, int(seed), n, _ptr(inst_ids), _ptr(pids), int(n_threads),
                           _ptr(out["prim"]), _ptr(out["cell"]), _ptr(out["E"]), _ptr(out["cos"]),
                           _ptr(out["ncoll"]), _ptr(out["score"]), _ptr(out["attempts"]),
@@ -229,13 +233,13 @@ class OracleScene:
         out["pid"] = pids
         return out
 
-    def run_all(self, n_threads=None, seed=None, score_T=False):
+    def run_all(self, n_threads=None, seed=None, score_T=False, at_cutoff=False):
         """Every particle of every instance, in ticket order (instance-major)."""
         ids, pids = [], []
         for i, I in enumerate(self.scene.instances):
             ids.append(np.full(int(I["n"]), i, np.int32))
             pids.append(np.arange(int(I["n"]), dtype=np.uint64))
-        return self.run_ids(np.concatenate(ids), np.concatenate(pids), n_threads, seed, score_T)
+        return self.run_ids(np.concatenate(ids), np.concatenate(pids), n_threads, seed, score_T, at_cutoff)
 
     def dlnK_dlns(self, cath, v):
         """d ln K / d ln s at speed v (s = per-axis thermal spread of the gas)."""
@@ -307,6 +311,10 @@ class OracleScene:
         mu, E = C.c_double(), C.c_double()
         lib().or_table_launch(self.h, int(cath), float(u_mu), float(u_E), C.byref(mu), C.byref(E))
         return mu.value, E.value
+
+    def set_at_cutoff(self, on):
+        """Launch at E = E_max in launch() and the runs that follow (boundary runs)."""
+        lib().or_scene_set_at_cutoff(self.h, 1 if on else 0)
 
     def launch(self, inst, pid, seed=None):
         p, d, E = np.zeros(3), np.zeros(3), np.zeros(1)

@@ -432,6 +432,7 @@ typedef struct or_scene {
     double chi_min;
     int interaction, gas_motion, max_attempts;
     int want_score_T; /* compute the temperature score (or_scene_set_score_T) */
+    int at_cutoff;    /* launch every atom with E = E_max (boundary run of d/dE_max) */
     int64_t max_collisions;
     double hs_diameter;
 } or_scene;
@@ -862,7 +863,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
     double E, mu;
     if (c->lt) table_launch(c, rn(w[3]), rn(w[2]), &mu, &E);
     else {
-        E = or_thompson(I->E_max, c->U_s, rn(w[2]));
+        E = S->at_cutoff ? I->E_max : or_thompson(I->E_max, c->U_s, rn(w[2]));
         mu = or_cos_mu(c->coef, rn(w[3]));
     }
     draw(&st, 0u, 1u, w);
@@ -1138,6 +1139,8 @@ int or_run_ids(const or_scene* S, uint64_t seed, int64_t n, const int32_t* inst,
 int or_version(void) { return OR_VERSION; }
 /* compute the temperature score in or_run_ids from now on (slower: three quadratures per flight) */
 void or_scene_set_score_T(or_scene* S, int on) { S->want_score_T = on; }
+/* launch every atom at the Thompson cut-off E_max from now on (boundary runs) */
+void or_scene_set_at_cutoff(or_scene* S, int on) { S->at_cutoff = on; }
 double or_dlnK_dlns(const or_scene* S, int cath, double v) { return dlnK_dlns(S, &S->cath[cath], v); }
 double or_c_energy(void) { return c_energy(); }
 double or_s_gas(const or_scene* S) { return S->s_gas; }
@@ -1203,7 +1206,7 @@ void or_launch(const or_scene* S, uint64_t seed, int ii, uint64_t pid, double* p
     double mu;
     if (c->lt) table_launch(c, rn(w[3]), rn(w[2]), &mu, E);
     else {
-        *E = or_thompson(I->E_max, c->U_s, rn(w[2]));
+        *E = S->at_cutoff ? I->E_max : or_thompson(I->E_max, c->U_s, rn(w[2]));
         mu = or_cos_mu(c->coef, rn(w[3]));
     }
     draw(&st, 0u, 1u, w);

@@ -179,6 +179,7 @@ class sput_tune_result(C.Structure):
 
 SPUT_RUN_NO_SMEM_COUNTERS = 1
 SPUT_RUN_SMEM_COUNTERS = 2
+SPUT_RUN_LAUNCH_AT_CUTOFF = 4
 
 ABI_STRUCTS = [sput_chamber, sput_primitive, sput_geometry, sput_cathode, sput_instance, sput_grid, sput_physics,
                sput_scene_desc, sput_record, sput_tallies, sput_tally_layout, sput_run_opts, sput_run_stats,
@@ -203,6 +204,7 @@ SIGNATURES = {
     "sput_graph_launch": (C.c_int, [_P, C.c_uint64, _P]),
     "sput_graph_destroy": (None, [_P]),
     "sput_backward": (C.c_int, [_P, _P, _P, _P, _P]),
+    "sput_emax_backward": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "sput_composition": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P]),
     "sput_composition_backward": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
                                             _P]),

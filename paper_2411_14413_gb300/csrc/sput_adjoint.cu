@@ -57,6 +57,38 @@ __global__ void lr_backward_kernel(const double* g, const double* score, double*
     }
 }
 
+// Derivative with respect to the Thompson cut-off.  The launch energy has the
+// density p(E) = E/(E+U)^3 / Z(E_max) on (0, E_max], Z = E_max^2 / (2U (E_max+U)^2),
+// so d ln p(E)/dE_max = -p(E_max) for every E inside the support, and the moving
+// end of the support adds p(E_max) E[f | E = E_max]:
+//   d E[f]/dE_max = p(E_max) (E[f | E = E_max] - E[f]),  p(E_max) = 2U / (E_max (E_max + U)).
+// With a boundary run of the same particles launched at E_max (counts_cut) and
+// dE_max/dE_i = k Lambda, one block per instance forms
+//   grad[i] = k Lambda p(E_max) sum_c g[i][c] (counts_cut[i][c] - counts[i][c]).
+template <typename CountT>
+__global__ void emax_backward_kernel(const double* g, const CountT* counts, const CountT* counts_cut,
+                                     const sput::DevInstance* inst, double* grad, long long n_cells)
+{
+    __shared__ double part[32];
+    const long long base = (long long)blockIdx.x * n_cells;
+    double s = 0.0;
+    for (long long c = threadIdx.x; c < n_cells; c += blockDim.x)
+        s += g[base + c] * ((double)counts_cut[base + c] - (double)counts[base + c]);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) {
+            const sput::DevInstance I = inst[blockIdx.x];
+            const double q = I.thompson_q, U = I.U_s;
+            const double Em = U * q / (1.0 - q);
+            grad[blockIdx.x] = (double)I.kLambda * 2.0 * U / (Em * (Em + U)) * t;
+        }
+    }
+}
+
 // N[j][m] = sum of counts of cathode j over the cells of patch m
 __global__ void patch_sum_kernel(const long long* counts, const int32_t* patch, double* N, int n_cath, int n_cells,
                                  int n_points)
@@ -177,6 +209,30 @@ sput_status sput_backward(const sput_scene* scene, const double* grad_counts, co
     const long long n_cells = (long long)L.nx * L.ny;
     lr_backward_kernel<<<L.n_instances, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(grad_counts, score_tally,
                                                                                         grad_log_pressure, n_cells);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return adj_fail(SPUT_ERR_CUDA, cudaGetErrorString(e));
+    return SPUT_OK;
+}
+
+sput_status sput_emax_backward(const sput_scene* scene, const double* grad_counts, const void* counts,
+                               const void* counts_cutoff, double* grad_ion_energy, void* stream)
+{
+    if (!scene || !grad_counts || !counts || !counts_cutoff || !grad_ion_energy)
+        return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    sput_tally_layout L;
+    sput_status st = sput_tally_layout_get(scene, &L);
+    if (st != SPUT_OK) return st;
+    const long long n_cells = (long long)L.nx * L.ny;
+    const sput::DevInstance* inst = sput::scene_device_instances(scene);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (L.count_type == SPUT_COUNT_INT64)
+        emax_backward_kernel<<<L.n_instances, 256, 0, s>>>(grad_counts, static_cast<const long long*>(counts),
+                                                           static_cast<const long long*>(counts_cutoff), inst,
+                                                           grad_ion_energy, n_cells);
+    else
+        emax_backward_kernel<<<L.n_instances, 256, 0, s>>>(grad_counts, static_cast<const int*>(counts),
+                                                           static_cast<const int*>(counts_cutoff), inst,
+                                                           grad_ion_energy, n_cells);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return adj_fail(SPUT_ERR_CUDA, cudaGetErrorString(e));
     return SPUT_OK;

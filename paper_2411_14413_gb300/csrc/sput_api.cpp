@@ -249,6 +249,12 @@ const char* sput_status_str(sput_status s)
 
 const char* sput_last_error(void) { return g_last_error.c_str(); }
 
+}  // extern "C"
+
+const sput::DevInstance* sput::scene_device_instances(const sput_scene* S) { return S ? S->base.inst : nullptr; }
+
+extern "C" {
+
 static sput_status pack_instances(sput_scene* S)
 {
     const double kT = kBoltzmannJ * S->chamber.gas_T;
@@ -271,6 +277,8 @@ static sput_status pack_instances(sput_scene* S)
         D.ng14 = (float)(I.pressure / kT * 1e-9 * 1e-14);
         D.thompson_q = (float)(Em / (Em + C.U_s));
         D.U_s = (float)C.U_s;
+        D.kLambda = (float)(I.k * 4.0 * S->chamber.gas_mass * C.mass /
+                            ((S->chamber.gas_mass + C.mass) * (S->chamber.gas_mass + C.mass)));
         D.ticket_begin = S->prefix[i];
         S->prefix[i + 1] = S->prefix[i] + I.n_particles;
     }
@@ -701,8 +709,14 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     if (threads < 32 || threads > 256 || threads % 32) return fail(SPUT_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
     int chunk = opts->ticket_chunk ? opts->ticket_chunk : S->def_chunk;
     if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
-    const int flags = opts->flags ? opts->flags : S->def_flags;
-    if (flags & ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS)) return fail(SPUT_ERR_INVALID_ARG, "unknown flags");
+    if (opts->flags & ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS | SPUT_RUN_LAUNCH_AT_CUTOFF))
+        return fail(SPUT_ERR_INVALID_ARG, "unknown flags");
+    const int cutoff = opts->flags & SPUT_RUN_LAUNCH_AT_CUTOFF;
+    const int fsm = opts->flags & (SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS);
+    const int flags = (fsm ? fsm : S->def_flags) | cutoff;
+    if (cutoff)
+        for (const sput_cathode& C : S->cathodes)
+            if (C.launch_table) return fail(SPUT_ERR_UNSUPPORTED, "launch at the cut-off needs Thompson cathodes only");
     const int bps_req = opts->blocks_per_sm ? opts->blocks_per_sm : S->def_bps;
 
     Params p = S->base;
@@ -724,6 +738,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     p.stats = scratch + 1;
     p.status = reinterpret_cast<unsigned int*>(scratch + 1 + kNumStats);
     p.smem_counters = (flags & SPUT_RUN_NO_SMEM_COUNTERS) ? 0 : S->smem_counters_fit;
+    p.launch_at_cutoff = cutoff ? 1 : 0;
 
     const TallySizes sz = tally_sizes(S);
     if (!opts->accumulate) {

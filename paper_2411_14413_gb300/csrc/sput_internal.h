@@ -96,7 +96,7 @@ struct alignas(16) DevInstance {
     float ng14;           // n_gas (mm^-3) * 1e-14: inverse mean free path = ng14 * K / v
     float thompson_q;     // E_max / (E_max + U_s)
     float U_s;
-    float pad;
+    float kLambda;        // d E_max / d E_i = k Lambda
     unsigned long long ticket_begin;
     unsigned long long pad2;
 };
@@ -146,6 +146,7 @@ struct Params {
     unsigned long long ticket_begin, ticket_end;
     int chunk;
     int smem_counters;                 // prim/timed-out counters privatised in shared memory
+    int launch_at_cutoff;              // launch energy = E_max (SPUT_RUN_LAUNCH_AT_CUTOFF)
     // scratch (library-owned device memory)
     unsigned long long* ticket_counter;
     unsigned long long* stats;         // [particles, landed, timed_out, flights, collisions, attempts]
@@ -166,6 +167,9 @@ int transport_launch(const Params& p, int count64, int blocks, int threads, size
 size_t transport_smem_bytes(const Params& p);
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem);
 int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev, double* y_dev, void* stream);
+
+// Device copy of the scene's instance table (for the adjoint kernels).
+const DevInstance* scene_device_instances(const sput_scene* scene);
 
 // Error text for sput_last_error from other translation units.
 void set_last_error(const char* msg);

@@ -275,7 +275,8 @@ __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t ins
     if (C.lt_off >= 0) {
         table_launch(P.lt_tab + C.lt_off, C.lt_nmu, C.lt_nE, C.lt_dE, rn(w0.w), rn(w0.z), mu, E);
     } else {
-        const float s = sqrtf(rn(w0.z)) * I.thompson_q;
+        // Thompson inverse CDF at u_E; E_max itself in a boundary run
+        const float s = P.launch_at_cutoff ? I.thompson_q : sqrtf(rn(w0.z)) * I.thompson_q;
         E = I.U_s * s / (1.0f - s);
         mu = cosine_sum_mu(C, rn(w0.w));
     }

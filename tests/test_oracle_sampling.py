@@ -246,3 +246,41 @@ def test_launch_table_cell_edges(oracle_mod):
     mu, E = osc.table_launch(0, 4.0 / 8.0 + 1e-9, 1.0)  # just past cell 0 -> cell 2 (cell 1 empty)
     assert mu > 2 / 3 and E == pytest.approx(20.0)
     osc.close()
+
+
+# ------------------------------------------- derivative with respect to E_max
+def test_thompson_cutoff_derivative_identity(oracle_mod):
+    """For the Thompson law on (0, E_max], d P(E > E0)/dE_max equals
+    p(E_max) (1 - P(E > E0)), p(E_max) = 2U/(E_max (E_max + U)): the LR term
+    -p(E_max) E[f] plus the moving-support term p(E_max) f(E_max).  Checked
+    against central differences of the normalised CDF by quadrature."""
+    U = 4.44
+
+    def p_above(E0, Em):
+        dens = lambda e: e / (e + U) ** 3
+        Z = integrate.quad(dens, 0.0, Em, epsabs=0, epsrel=1e-13)[0]
+        return integrate.quad(dens, E0, Em, epsabs=0, epsrel=1e-13)[0] / Z
+
+    for Em in (20.0, 149.78):
+        # p(E_max) is the normalised density at the cut-off
+        Z = integrate.quad(lambda e: e / (e + U) ** 3, 0.0, Em, epsabs=0, epsrel=1e-13)[0]
+        pE = 2 * U / (Em * (Em + U))
+        assert abs(Em / (Em + U) ** 3 / Z - pE) < 1e-12 * pE
+        for E0 in (1.0, 5.0, 0.5 * Em):
+            h = 1e-4 * Em
+            fd = (p_above(E0, Em + h) - p_above(E0, Em - h)) / (2 * h)
+            assert abs(fd - pE * (1 - p_above(E0, Em))) < 1e-7 * pE, (Em, E0)
+
+
+def test_oracle_launch_at_cutoff(oracle_mod):
+    """The boundary run changes only the launch energy: E = E_max, same point and direction."""
+    sc = workloads.scene_single_ni(n=10)
+    o = oracle_mod.OracleScene(sc)
+    Em = o.emax(0)
+    for pid in range(5):
+        p, d, E = o.launch(0, pid)
+        o.set_at_cutoff(True)
+        pc, dc, Ec = o.launch(0, pid)
+        o.set_at_cutoff(False)
+        assert np.array_equal(p, pc) and np.array_equal(d, dc)
+        assert E < Em and Ec == Em
