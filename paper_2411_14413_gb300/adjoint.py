@@ -27,9 +27,15 @@ def _ptr(t):
 
 
 class MapSetup:
-    """Transport scene + measurement patches + calibration for one composition map."""
+    """Transport scene + measurement patches + calibration for one composition map.
 
-    def __init__(self, scene, patch_of_cell, ref_point, calibration, device=0):
+    voltage (optional, host [n_cath][4] = P_a, V_a, P_b, V_b): the discharge
+    voltage of each cathode as the line through two (power, voltage) points
+    (Table S1); the incident ion energy E_i (eV, singly charged ions) then
+    follows the power, which moves the Thompson cut-off E_max = k Lambda E_i - U_s,
+    and backward() adds that path to dL/dP (boundary run + sput_emax_backward)."""
+
+    def __init__(self, scene, patch_of_cell, ref_point, calibration, device=0, voltage=None):
         import torch
 
         self.scene = scene
@@ -49,20 +55,40 @@ class MapSetup:
         self.grad_logp = torch.zeros(self.n_cath, dtype=torch.float64, device=dev)
         self.grad_power = torch.zeros(self.n_cath, dtype=torch.float64, device=dev)
         self.comp = torch.zeros((self.n_points, self.n_cath), dtype=torch.float64, device=dev)
+        self.volt = None if voltage is None else np.ascontiguousarray(voltage, dtype=np.float64).reshape(self.n_cath, 4)
+        self.seed = None
+        if self.volt is not None:
+            self.counts_cut = torch.zeros_like(self.tr.t["counts"])
+            self._cut_tal = N.sput_tallies()
+            self._cut_tal.counts = self.counts_cut.data_ptr()
+            self.grad_Ei = torch.zeros(self.n_cath, dtype=torch.float64, device=dev)
+            self.dV_dP = torch.as_tensor((self.volt[:, 3] - self.volt[:, 1]) / (self.volt[:, 2] - self.volt[:, 0]),
+                                         dtype=torch.float64, device=dev)
 
     def stream(self):
         import torch
 
         return torch.cuda.current_stream(self.device).cuda_stream
 
-    def set_pressure(self, p):
+    def ion_energy(self, power):
+        """E_i (eV) of every cathode at the given powers, from the voltage lines."""
+        v = self.volt
+        return v[:, 1] + (v[:, 3] - v[:, 1]) * (np.asarray(power, float) - v[:, 0]) / (v[:, 2] - v[:, 0])
+
+    def set_conditions(self, p, power=None):
         sc = self.scene.with_pressure(float(p))
+        if self.volt is not None and power is not None:
+            sc = sc.with_ion_energy(self.ion_energy(power))
         self.scene = sc
         self.tr.set_instances(sc)
 
+    def set_pressure(self, p):
+        self.set_conditions(p)
+
     def forward(self, p, power, seed):
         """composition[n_points][n_cath] (at.%) for pressure p and powers (host array)."""
-        self.set_pressure(p)
+        self.set_conditions(p, power)
+        self.seed = seed
         self.tr.run(seed=seed, want_stats=False)
         pw = np.ascontiguousarray(power, dtype=np.float64)
         rc = N.load().sput_composition(self.n_cath, self.n_cells, self.n_points, _ptr(self.tr.t["counts"]),
@@ -85,6 +111,14 @@ class MapSetup:
         rc = L.sput_backward(self.tr.h, _ptr(self.grad_counts), _ptr(self.tr.t["score"]), _ptr(self.grad_logp),
                              C.c_void_p(self.stream()))
         N.check(rc, "sput_backward")
+        if self.volt is not None:
+            # the same particles launched at E_max: the moving end of the Thompson support
+            o = api.run_opts(seed=self.seed, flags=N.SPUT_RUN_LAUNCH_AT_CUTOFF)
+            api.sput_run(self.tr.h, o, self.stream(), self._cut_tal, False)
+            rc = L.sput_emax_backward(self.tr.h, _ptr(self.grad_counts), _ptr(self.tr.t["counts"]),
+                                      _ptr(self.counts_cut), _ptr(self.grad_Ei), C.c_void_p(self.stream()))
+            N.check(rc, "sput_emax_backward")
+            self.grad_power.add_(self.grad_Ei * self.dV_dP)
         return self.grad_logp, self.grad_power
 
     def close(self):

@@ -26,6 +26,13 @@ TABLE_S1 = {
     "Pt": {"DC": [(5.0, 9960.0, 140.5, 0.01411), (35.0, 960.0, 102.4, 0.1067)]},
     "Ru": {"DC": [(5.0, 18000.0, 97.6, 0.005422), (35.0, 1800.0, 90.5, 0.05028)]},
 }
+# element -> supply -> [(power W, discharge voltage V)], the voltage column of Table S1
+VOLTAGE_S1 = {
+    "Ni": {"DC": [(5.0, 289.0), (35.0, 294.0)], "RF": [(7.0, 25.0), (30.0, 33.0)]},
+    "Pd": {"DC": [(5.0, 294.0), (30.0, 299.0)], "RF": [(7.0, 29.0), (60.0, 49.0)]},
+    "Pt": {"DC": [(5.0, 306.0), (35.0, 323.0)]},
+    "Ru": {"DC": [(5.0, 262.0), (35.0, 272.0)]},
+}
 # supply pairing of Table 1 (all libraries but the equiatomic one)
 SUPPLY = {"Ni": "DC", "Pd": "RF", "Pt": "DC", "Ru": "DC"}
 # power set-points of Table 1 per element (W), the range the synthetic targets are drawn from
@@ -58,3 +65,9 @@ def measurement_patches(nx=200, ny=200, half_u=50.0, half_v=50.0, pitch=4.0, dia
             patch[y * nx + ix] = m
     ref = int(np.argmin(pts[:, 0] ** 2 + pts[:, 1] ** 2))
     return patch, pts, ref
+
+
+def voltage_points(symbol: str):
+    """The two (power W, voltage V) points of Table S1 for the element's supply
+    (DC: discharge voltage; RF: bias)."""
+    return list(VOLTAGE_S1[symbol][SUPPLY[symbol]])

@@ -71,6 +71,15 @@ class Scene:
         s.physics.update(kw)
         return s
 
+    def with_ion_energy(self, E_i) -> "Scene":
+        """Copy with the incident ion energy (eV) of every instance set (scalar or list)."""
+        import copy
+        s = copy.deepcopy(self)
+        es = E_i if isinstance(E_i, (list, tuple, np.ndarray)) else [E_i] * len(s.instances)
+        for inst, e in zip(s.instances, es):
+            inst["E_i"] = float(e)
+        return s
+
     def with_pressure(self, p) -> "Scene":
         import copy
         s = copy.deepcopy(self)
