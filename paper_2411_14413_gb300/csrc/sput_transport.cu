@@ -667,7 +667,7 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
 }
 
 template <bool kCount64, bool kScoreT>
-__global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
+__global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout L = smem_layout(P);
