@@ -64,7 +64,7 @@
 extern "C" {
 #endif
 
-#define SPUT_ABI_VERSION 3
+#define SPUT_ABI_VERSION 4
 
 typedef enum sput_status {
     SPUT_OK = 0,
@@ -168,6 +168,13 @@ typedef struct sput_physics {
     int max_attempts;            /* partner rejection attempts per collision, 1..64 */
     int reserved;
     int64_t max_collisions;      /* per particle; beyond it the atom counts as timed out */
+    double thermal_switch_eV;    /* diffusion shortcut for thermalised atoms (0 = off, the exact model):
+                                    once a collision leaves the atom below this energy, it moves on as
+                                    an isotropic random walk with exponential steps of mean
+                                    lambda_D = 3 D_12 / vbar_1 (D_12 the first Chapman-Enskog diffusion
+                                    coefficient from the momentum-transfer cross section, vbar_1 the mean
+                                    thermal speed of the atom), speed frozen; thermal gas only; not
+                                    combined with the temperature score */
 } sput_physics;
 
 typedef struct sput_scene_desc {

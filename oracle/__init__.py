@@ -90,7 +90,7 @@ def lib():
                 "or_c_energy": [], "or_s_gas": [p], "or_n_gas": [p, i], "or_inst_emax": [p, i],
                 "or_cath_ascr": [p, i], "or_sigma": [p, i, d], "or_K": [p, i, d], "or_M": [p, i, d],
                 "or_lambda": [p, i, d], "or_rel_speed_pdf": [d, d, d], "or_integrate_test": [i, d, d],
-                "or_dlnK_dlns": [p, i, d],
+                "or_dlnK_dlns": [p, i, d], "or_sigma_m": [p, i, d], "or_sigma_D": [p, i],
             }.items():
                 f = getattr(L, name)
                 f.restype = d
@@ -165,7 +165,8 @@ def _flatten(scene):
                      g["n_abins"], 0.0], float)
     ph = scene.physics
     phys = np.array([math.radians(ph["chi_min_deg"]), INTERACTION[ph["interaction"]], ph["hs_diameter"],
-                     GAS_MOTION[ph["gas_motion"]], ph["max_attempts"], ph["max_collisions"], 0.0, 0.0], float)
+                     GAS_MOTION[ph["gas_motion"]], ph["max_attempts"], ph["max_collisions"],
+                     ph.get("thermal_switch_eV", 0.0), 0.0], float)
     return ch, prims, geoms, cath, inst, grid, phys
 
 
@@ -240,6 +241,14 @@ class OracleScene:
             ids.append(np.full(int(I["n"]), i, np.int32))
             pids.append(np.arange(int(I["n"]), dtype=np.uint64))
         return self.run_ids(np.concatenate(ids), np.concatenate(pids), n_threads, seed, score_T, at_cutoff)
+
+    def sigma_m(self, cath, g):
+        """Momentum-transfer cross section (Angstrom^2) at relative speed g (km/s)."""
+        return lib().or_sigma_m(self.h, int(cath), float(g))
+
+    def sigma_D(self, cath):
+        """Diffusion cross section (Angstrom^2) of the shortcut: 1/lambda_D = n sigma_D."""
+        return lib().or_sigma_D(self.h, int(cath))
 
     def dlnK_dlns(self, cath, v):
         """d ln K / d ln s at speed v (s = per-axis thermal spread of the gas)."""

@@ -410,6 +410,7 @@ typedef struct {
     int n_mu, n_E;
     double E_hi;
     double* lt;
+    double sigma_D; /* diffusion cross section of the shortcut, Angstrom^2 (set when E_switch > 0) */
 } cath_t;
 
 typedef struct {
@@ -433,6 +434,7 @@ typedef struct or_scene {
     int interaction, gas_motion, max_attempts;
     int want_score_T; /* compute the temperature score (or_scene_set_score_T) */
     int at_cutoff;    /* launch every atom with E = E_max (boundary run of d/dE_max) */
+    double E_switch;  /* eV: diffusion shortcut below it (0 = off) */
     int64_t max_collisions;
     double hs_diameter;
 } or_scene;
@@ -538,6 +540,55 @@ static double M_of_v(const or_scene* S, const cath_t* c, double v)
         if (hv > m) m = hv;
     }
     return m;
+}
+
+/* ---------------------------------------------- diffusion shortcut (opt-in) */
+typedef struct {
+    const or_scene* S;
+    const cath_t* c;
+    double eps, gpy;
+} sm_ctx;
+
+static double sm_integrand(double beta, const void* vctx)
+{
+    const sm_ctx* k = (const sm_ctx*)vctx;
+    double h = sin(0.5 * or_chi(0, k->eps, beta));
+    return 2.0 * h * h * beta; /* (1 - cos chi) beta */
+}
+
+/* momentum-transfer cross section sigma_m(g) = 2 pi int_0^inf (1 - cos chi) b db, Angstrom^2 */
+static double sigma_m_of_g(const or_scene* S, const cath_t* c, double g)
+{
+    if (S->interaction == INT_HARD_SPHERE) return M_PI * S->hs_diameter * S->hs_diameter;
+    double eps = c->a_scr * 0.5 * c->mu_red * g * g * c_energy() / c->zze2;
+    if (!(eps > 1e-40)) eps = 1e-40;
+    double B = or_bmax_interp(S->chi_min, eps);
+    if (B < 1.0) B = 1.0;
+    while (or_chi(0, eps, B) > 1e-9 && B < 1e4) B *= 1.5;
+    sm_ctx k = {S, c, eps, 0.0};
+    double I = 0.0;
+    for (int p = 0; p < 16; ++p) I += integrate(sm_integrand, &k, B * p / 16.0, B * (p + 1) / 16.0, 1e-10);
+    return 2.0 * M_PI * c->a_scr * c->a_scr * I;
+}
+
+static double om_integrand(double y, const void* vctx)
+{
+    const sm_ctx* k = (const sm_ctx*)vctx;
+    return exp(-y * y) * pow(y, 5) * sigma_m_of_g(k->S, k->c, y * k->gpy);
+}
+
+/* 1/lambda_D = n sigma_D with lambda_D = 3 D12 / vbar1: D12 = 3kT/(16 n mu Omega11) is the first
+ * Chapman-Enskog diffusion coefficient, Omega11 = sqrt(kT/(2 pi mu)) int e^{-y^2} y^5 sigma_m dy
+ * with g = y sqrt(2kT/mu), vbar1 = sqrt(8kT/(pi m1)) the atom's mean thermal speed; Angstrom^2 */
+static double sigma_D_of(const or_scene* S, const cath_t* c)
+{
+    double kT = KB_J * S->T, mu = c->mu_red * AMU_KG;
+    sm_ctx k = {S, c, 0.0, sqrt(2.0 * kT / mu) * 1e-3};
+    double I = 0.0;
+    for (int p = 0; p < 12; ++p) I += integrate(om_integrand, &k, 0.5 * p, 0.5 * (p + 1), 1e-10);
+    double omega = sqrt(kT / (2.0 * M_PI * mu)) * I;
+    double vbar1 = sqrt(8.0 * kT / (M_PI * c->mass * AMU_KG));
+    return 16.0 * mu * vbar1 * omega / (9.0 * kT);
 }
 
 /* ----------------------------------------------------------------- sampling */
@@ -876,13 +927,14 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
     }
     double speed = speed_of_E(E, c->mass);
     int64_t ncoll = 0, attempts = 0;
+    int walk = 0; /* thermalised: random walk of the diffusion shortcut */
     double score = 0.0, score_T = 0.0;
     o->score_T = 0.0;
     trace_row(tr, rows, 0, p, d, speed, -1, 0.0, 0.0);
 
     for (uint32_t k = 1;; ++k) {
         draw(&st, k, 0u, w);
-        double lam = lambda_m(S, c, I, speed);
+        double lam = walk ? 1.0 / (I->n_gas * c->sigma_D * 1e-14) : lambda_m(S, c, I, speed);
         /* no gas (p = 0): straight line-of-sight flight */
         double ell = I->n_gas > 0.0 ? -lam * log(rn(w[0])) : INFINITY;
         double t;
@@ -938,6 +990,17 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
             o->attempts = attempts;
             return;
         }
+        if (walk) {
+            /* isotropic new direction from words 1 and 2; speed unchanged */
+            double mu = 2.0 * rn(w[1]) - 1.0, phi = 2.0 * M_PI * rn(w[2]);
+            double sn = sqrt((1.0 - mu) * (1.0 + mu));
+            d[0] = sn * cos(phi);
+            d[1] = sn * sin(phi);
+            d[2] = mu;
+            ++ncoll;
+            trace_row(tr, rows, (int)k, p, d, speed, 0, 0.0, ell);
+            continue;
+        }
         for (int a = 0; a < 3; ++a) v[a] = speed * d[a];
         double V[3], vo[3], Vo[3];
         int na = sample_partner(S, c, &st, k, v, V);
@@ -949,6 +1012,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
         speed = sqrt(dot3(vo, vo));
         for (int a = 0; a < 3; ++a) d[a] = vo[a] / speed;
         ++ncoll;
+        if (S->E_switch > 0.0 && 0.5 * c->mass * speed * speed * c_energy() < S->E_switch) walk = 1;
         trace_row(tr, rows, (int)k, p, d, speed, 0, na, ell);
     }
 }
@@ -983,6 +1047,7 @@ or_scene* or_scene_new(const double* chamber, int n_prims, const double* prims, 
     S->gas_motion = (int)phys[3];
     S->max_attempts = (int)phys[4];
     S->max_collisions = (int64_t)phys[5];
+    S->E_switch = phys[6];
     S->nx = (int)grid[0];
     S->ny = (int)grid[1];
     S->half_u = grid[2];
@@ -1048,6 +1113,7 @@ or_scene* or_scene_new(const double* chamber, int n_prims, const double* prims, 
         const cath_t* c = &S->cath[I->cathode];
         I->E_max = or_emax(I->k, S->gas_mass, c->mass, I->E_i, c->U_s);
     }
+    for (int i = 0; i < n_cath; ++i) S->cath[i].sigma_D = S->E_switch > 0.0 ? sigma_D_of(S, &S->cath[i]) : 0.0;
     /* check monotonicity of sigma(g) g up to well beyond the fastest launch */
     for (int i = 0; i < n_cath; ++i) {
         cath_t* c = &S->cath[i];
@@ -1142,6 +1208,8 @@ void or_scene_set_score_T(or_scene* S, int on) { S->want_score_T = on; }
 /* launch every atom at the Thompson cut-off E_max from now on (boundary runs) */
 void or_scene_set_at_cutoff(or_scene* S, int on) { S->at_cutoff = on; }
 double or_dlnK_dlns(const or_scene* S, int cath, double v) { return dlnK_dlns(S, &S->cath[cath], v); }
+double or_sigma_m(const or_scene* S, int cath, double g) { return sigma_m_of_g(S, &S->cath[cath], g); }
+double or_sigma_D(const or_scene* S, int cath) { return sigma_D_of(S, &S->cath[cath]); }
 double or_c_energy(void) { return c_energy(); }
 double or_s_gas(const or_scene* S) { return S->s_gas; }
 double or_n_gas(const or_scene* S, int inst) { return S->inst[inst].n_gas; }

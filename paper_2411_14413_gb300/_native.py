@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # --------------------------------------------------------------- ABI mirror
-SPUT_ABI_VERSION = 3
+SPUT_ABI_VERSION = 4
 SPUT_OK = 0
 STATUS_NAMES = {0: "SPUT_OK", 1: "SPUT_ERR_INVALID_ARG", 2: "SPUT_ERR_INVALID_SCENE", 3: "SPUT_ERR_CUDA",
                 4: "SPUT_ERR_TIMEOUT", 5: "SPUT_ERR_DEVICE_CHECK", 6: "SPUT_ERR_UNSUPPORTED", 7: "SPUT_ERR_NO_MEMORY"}
@@ -123,7 +123,7 @@ class sput_grid(C.Structure):
 class sput_physics(C.Structure):
     _fields_ = [("chi_min", C.c_double), ("hs_diameter", C.c_double), ("interaction", C.c_int),
                 ("gas_motion", C.c_int), ("max_attempts", C.c_int), ("reserved", C.c_int),
-                ("max_collisions", C.c_int64)]
+                ("max_collisions", C.c_int64), ("thermal_switch_eV", C.c_double)]
 
 
 class sput_scene_desc(C.Structure):

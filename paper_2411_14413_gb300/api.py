@@ -82,6 +82,7 @@ def scene_desc(scene):
     d.physics.gas_motion = N.GAS_MOTION[ph["gas_motion"]]
     d.physics.max_attempts = ph["max_attempts"]
     d.physics.max_collisions = ph["max_collisions"]
+    d.physics.thermal_switch_eV = float(ph.get("thermal_switch_eV", 0.0))
     return d, (prims, geoms, cath, inst, keep)
 
 

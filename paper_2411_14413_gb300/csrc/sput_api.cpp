@@ -200,6 +200,10 @@ sput_status validate(const sput_scene_desc* d)
     if (ph.gas_motion != SPUT_GAS_THERMAL && ph.gas_motion != SPUT_GAS_STATIONARY) return fail(SPUT_ERR_INVALID_SCENE, "bad gas_motion");
     if (ph.max_attempts < 1 || ph.max_attempts > 64) return fail(SPUT_ERR_INVALID_SCENE, "max_attempts must be 1..64");
     if (ph.max_collisions < 0 || ph.max_collisions > 0xFFFFFFF0LL) return fail(SPUT_ERR_INVALID_SCENE, "max_collisions out of range");
+    if (!(ph.thermal_switch_eV >= 0.0) || !std::isfinite(ph.thermal_switch_eV))
+        return fail(SPUT_ERR_INVALID_SCENE, "thermal_switch_eV must be >= 0");
+    if (ph.thermal_switch_eV > 0.0 && ph.gas_motion != SPUT_GAS_THERMAL)
+        return fail(SPUT_ERR_INVALID_SCENE, "the diffusion shortcut needs a thermal gas");
     return SPUT_OK;
 }
 
@@ -413,6 +417,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         S->wtab.insert(S->wtab.end(), M.begin(), M.end());
         D.G_off = (int)S->wtab.size();
         S->wtab.insert(S->wtab.end(), Gt.begin(), Gt.end());
+        D.sigma_D = S->physics.thermal_switch_eV > 0.0 ? (float)sigma_D64(pp, S->bt, S->chamber.gas_T) : 0.0f;
+        D.pad_d[0] = D.pad_d[1] = D.pad_d[2] = 0.0f;
         D.n_w = n_w;
         D.w_inv_h = (float)(1.0 / h_w);
         D.inv_s = (float)(1.0 / S->s_gas);
@@ -583,6 +589,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     }
     p.s_gas = (float)S->s_gas;
     p.inv_T = (float)(1.0 / S->chamber.gas_T);
+    p.E_switch = (float)S->physics.thermal_switch_eV;
     p.inv_s2 = (float)(1.0 / (S->s_gas * S->s_gas));
     p.gas_thermal = thermal;
     p.max_attempts = S->physics.max_attempts;
@@ -714,6 +721,8 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     const int cutoff = opts->flags & SPUT_RUN_LAUNCH_AT_CUTOFF;
     const int fsm = opts->flags & (SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS);
     const int flags = (fsm ? fsm : S->def_flags) | cutoff;
+    if (T->score_T && S->physics.thermal_switch_eV > 0.0)
+        return fail(SPUT_ERR_UNSUPPORTED, "the temperature score is not defined with the diffusion shortcut");
     if (cutoff)
         for (const sput_cathode& C : S->cathodes)
             if (C.launch_table) return fail(SPUT_ERR_UNSUPPORTED, "launch at the cut-off needs Thompson cathodes only");

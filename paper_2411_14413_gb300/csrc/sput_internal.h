@@ -88,6 +88,8 @@ struct alignas(16) DevPair {
     float w_inv_h;      // 1 / Delta w
     float inv_s;        // 1 / s_gas, w = ln(1 + v / s_gas)
     int G_off;          // float4 offset of the d ln K / d ln s table (zero for a gas at rest)
+    float sigma_D;      // diffusion cross section (A^2) of the thermalised-atom shortcut: 1/lambda_D = n sigma_D
+    float pad_d[3];
 };
 
 struct alignas(16) DevInstance {
@@ -147,6 +149,7 @@ struct Params {
     int chunk;
     int smem_counters;                 // prim/timed-out counters privatised in shared memory
     int launch_at_cutoff;              // launch energy = E_max (SPUT_RUN_LAUNCH_AT_CUTOFF)
+    float E_switch;                    // eV; below it after a collision the atom turns diffusive (0 = off)
     // scratch (library-owned device memory)
     unsigned long long* ticket_counter;
     unsigned long long* stats;         // [particles, landed, timed_out, flights, collisions, attempts]

@@ -337,6 +337,51 @@ void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s, int therm
     }
 }
 
+double sigma_m64(const PairPhys& pp, const BmaxTable* bt, double g)
+{
+    if (pp.hard_sphere) return kPi * pp.hs_d * pp.hs_d;  // isotropic CM scattering: sigma_m = sigma
+    // 1 - cos chi = 2 sin^2(chi/2) over beta = b/a, out to where chi < 1e-9 rad
+    const double eps = std::max(pp.kappa * g * g, 1e-40);
+    double B = std::max(1.0, bt->eval(std::log(eps)));
+    while (chi_moliere64(eps, B) > 1e-9 && B < 1e4) B *= 1.5;
+    const GL& G = gl24();
+    const int panels = 24;
+    double sum = 0.0;
+    for (int p = 0; p < panels; ++p) {
+        double x0 = B * p / panels, x1 = B * (p + 1) / panels;
+        double hm = 0.5 * (x1 - x0), mm = 0.5 * (x1 + x0);
+        for (size_t i = 0; i < G.x.size(); ++i) {
+            double beta = mm + hm * G.x[i];
+            double sh = std::sin(0.5 * chi_moliere64(eps, beta));
+            sum += hm * G.w[i] * 2.0 * sh * sh * beta;
+        }
+    }
+    return 2.0 * kPi * pp.a * pp.a * sum;
+}
+
+double sigma_D64(const PairPhys& pp, const BmaxTable* bt, double T)
+{
+    const double kT = kBoltzmannJ * T;
+    const double mu = pp.m1 * pp.m2 / (pp.m1 + pp.m2) * kAmuKg;        // kg
+    const double g_per_y = std::sqrt(2.0 * kT / mu) * 1e-3;             // km/s per unit y
+    // Omega11 / sqrt(kT/(2 pi mu)) = int_0^inf e^{-y^2} y^5 sigma_m dy on [0, 6] (Angstrom^2;
+    // the rest of the range weighs below 1e-12)
+    const GL& G = gl24();
+    const int panels = 8;
+    double I = 0.0;
+    for (int p = 0; p < panels; ++p) {
+        double y0 = 6.0 * p / panels, y1 = 6.0 * (p + 1) / panels;
+        double hm = 0.5 * (y1 - y0), mm = 0.5 * (y1 + y0);
+        for (size_t i = 0; i < G.x.size(); ++i) {
+            double y = mm + hm * G.x[i];
+            I += hm * G.w[i] * std::exp(-y * y) * std::pow(y, 5) * sigma_m64(pp, bt, y * g_per_y);
+        }
+    }
+    const double omega = std::sqrt(kT / (2.0 * kPi * mu)) * I;          // Angstrom^2 m/s
+    const double vbar1 = std::sqrt(8.0 * kT / (kPi * pp.m1 * kAmuKg));  // m/s
+    return 16.0 * mu * vbar1 * omega / (9.0 * kT);                       // Angstrom^2
+}
+
 double racetrack_F64(double r0, double sg, double r)
 {
     // integral of rho exp(-(rho-r0)^2/(2 sg^2)) over [0, r]

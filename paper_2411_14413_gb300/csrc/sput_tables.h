@@ -62,6 +62,13 @@ double sigma64(const PairPhys& pp, const BmaxTable* bt, double g);
 void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v_top,
                     double h_w, std::vector<float4>& K, std::vector<float4>& M, std::vector<float4>& G, int& n_w);
 
+// Momentum-transfer cross section sigma_m(g) = 2 pi int_0^inf (1 - cos chi) b db (Angstrom^2)
+// and the diffusion cross section sigma_D (Angstrom^2) of the shortcut for thermalised atoms:
+// 1/lambda_D = n sigma_D with lambda_D = 3 D_12 / vbar_1, D_12 = 3 kT / (16 n mu Omega11),
+// Omega11 = sqrt(kT / (2 pi mu)) int_0^inf exp(-y^2) y^5 sigma_m(y sqrt(2kT/mu)) dy.
+double sigma_m64(const PairPhys& pp, const BmaxTable* bt, double g);
+double sigma_D64(const PairPhys& pp, const BmaxTable* bt, double T);
+
 // FP64 host values used by tests through the probe entry point.
 double K64(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v);
 double M64(const PairPhys& pp, const BmaxTable* bt, double s_gas, double v, int monotone);

@@ -192,6 +192,7 @@ __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& b1, fl
 struct Lane {
     float px, py, pz, dx, dy, dz, speed, score;
     float scoreT;  // d ln p(path)/dT (kernel instance with the temperature score only)
+    bool diff;     // thermalised: random walk of the diffusion shortcut
     uint32_t pid, inst, k, ncoll;
     int gbegin, gcount, gsub, target, pair;
     float ng14, E_per_v2;
@@ -366,6 +367,7 @@ __device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, u
     S.ncoll = 0u;
     S.score = 0.0f;
     S.scoreT = 0.0f;
+    S.diff = false;
 }
 
 // ------------------------------------------------------------- one flight
@@ -395,7 +397,8 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     const DevPair pr = pairs[S.pair];
     // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
     const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
-    const float inv_lam = P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv;
+    // (diffusion shortcut: exponential steps of mean lambda_D, 1/lambda_D = n sigma_D)
+    const float inv_lam = S.diff ? S.ng14 * pr.sigma_D : (P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv);
     const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
     // temperature score: d ln(n_g K(v)/v)/dT = (-1 + G/2)/T with n_g = p/(k_B T), G = d ln K/d ln s
     float aT = 0.0f;
@@ -607,7 +610,9 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
     out.attempts = 0;
     if (kScoreT) out.Gv = 0.0f;
     if (active) res = flight_move<kScoreT>(S, P, T, prims, pairs, out, w);
-    const bool coll = res == kStepCollided;
+    // a thermalised atom (diffusion shortcut) turns isotropically at the end of its step
+    const bool walk = res == kStepCollided && S.diff;
+    const bool coll = res == kStepCollided && !S.diff;
     const DevPair pr = pairs[S.pair];
     const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
     float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
@@ -619,7 +624,20 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
         if (kScoreT && coll)
             S.scoreT += (0.5f * (Vx * Vx + Vy * Vy + Vz * Vz) * P.inv_s2 - 1.5f - 0.5f * out.Gv) * P.inv_T;
     }
-    if (coll) scatter(S, P, T, pr, vx, vy, vz, Vx, Vy, Vz, w);
+    if (coll) {
+        scatter(S, P, T, pr, vx, vy, vz, Vx, Vy, Vz, w);
+        if (P.E_switch > 0.0f && S.E_per_v2 * S.speed * S.speed < P.E_switch) S.diff = true;
+    } else if (walk) {
+        // isotropic direction from the flight block's words 1 and 2
+        const float mu = 2.0f * rn(w.y) - 1.0f;
+        const float st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
+        float sp, cp;
+        sincospif(2.0f * rn(w.z), &sp, &cp);
+        S.dx = st * cp;
+        S.dy = st * sp;
+        S.dz = mu;
+        ++S.ncoll;
+    }
     return res;
 }
 

@@ -97,6 +97,7 @@ def default_physics(**kw) -> dict:
         "gas_motion": "thermal",     # "thermal" | "stationary"
         "max_attempts": 32,          # partner rejection attempts per collision
         "max_collisions": 1_000_000, # per particle; beyond it the particle is counted as timed out
+        "thermal_switch_eV": 0.0,    # diffusion shortcut for thermalised atoms below this energy (0 = off)
     }
     phys.update(kw)
     return phys
