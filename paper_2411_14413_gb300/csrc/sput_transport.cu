@@ -23,6 +23,9 @@ namespace sput {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// kernel instances: the exact transport, with the temperature score, or with the
+// diffusion shortcut for thermalised atoms (the two options exclude each other)
+enum { kModePlain = 0, kModeScoreT = 1, kModeWalk = 2 };
 // dead lanes of a warp that trigger a refill (measured optimum 4-8 on the
 // quaternary workload; 1 = refill every flight)
 constexpr int kRefillMin = 6;
@@ -385,7 +388,7 @@ struct StepOut {
 // pre-flight position and out.t is the hit distance.  Otherwise the atom moves
 // to the collision point; w is the flight's Philox block (words 1 and 2, the
 // impact parameter and azimuth, are used by the collision; word 3 is unused).
-template <bool kScoreT>
+template <int kMode>
 __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
                            StepOut& out, uint4& w)
 {
@@ -397,8 +400,10 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     const DevPair pr = pairs[S.pair];
     // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
     const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
-    // (diffusion shortcut: exponential steps of mean lambda_D, 1/lambda_D = n sigma_D)
-    const float inv_lam = S.diff ? S.ng14 * pr.sigma_D : (P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv);
+    float inv_lam = P.gas_thermal ? S.ng14 * Kv / S.speed : S.ng14 * Kv;
+    // diffusion shortcut: exponential steps of mean lambda_D, 1/lambda_D = n sigma_D
+    if (kMode == kModeWalk && S.diff) inv_lam = S.ng14 * pr.sigma_D;
+    constexpr bool kScoreT = kMode == kModeScoreT;
     const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
     // temperature score: d ln(n_g K(v)/v)/dT = (-1 + G/2)/T with n_g = p/(k_B T), G = d ln K/d ln s
     float aT = 0.0f;
@@ -601,18 +606,19 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
 // One flight of every active lane of the warp (flight, surface test, then for
 // the lanes that collide: warp-wide partner sampling and the scattering).
 // Must be called by all 32 lanes together; inactive lanes return kStepNone.
-template <bool kScoreT>
+template <int kMode>
 __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const TableView& T, const DevPrim* prims,
                                 const DevPair* pairs, StepOut& out)
 {
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
     int res = kStepNone;
     out.attempts = 0;
+    constexpr bool kScoreT = kMode == kModeScoreT;
     if (kScoreT) out.Gv = 0.0f;
-    if (active) res = flight_move<kScoreT>(S, P, T, prims, pairs, out, w);
+    if (active) res = flight_move<kMode>(S, P, T, prims, pairs, out, w);
     // a thermalised atom (diffusion shortcut) turns isotropically at the end of its step
-    const bool walk = res == kStepCollided && S.diff;
-    const bool coll = res == kStepCollided && !S.diff;
+    const bool walk = kMode == kModeWalk && res == kStepCollided && S.diff;
+    const bool coll = res == kStepCollided && !walk;
     const DevPair pr = pairs[S.pair];
     const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
     float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
@@ -626,7 +632,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
     }
     if (coll) {
         scatter(S, P, T, pr, vx, vy, vz, Vx, Vy, Vz, w);
-        if (P.E_switch > 0.0f && S.E_per_v2 * S.speed * S.speed < P.E_switch) S.diff = true;
+        if (kMode == kModeWalk && S.E_per_v2 * S.speed * S.speed < P.E_switch) S.diff = true;
     } else if (walk) {
         // isotropic direction from the flight block's words 1 and 2
         const float mu = 2.0f * rn(w.y) - 1.0f;
@@ -684,7 +690,7 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
     for (size_t i = (bytes / 16) * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
 }
 
-template <bool kCount64, bool kScoreT>
+template <bool kCount64, int kMode>
 __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -781,7 +787,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
 
         // ---------------------------------------------------- one flight (all lanes together)
         StepOut so;
-        const int res = flight_step_warp<kScoreT>(alive, S, P, T, s_prims, s_pairs, so);
+        const int res = flight_step_warp<kMode>(alive, S, P, T, s_prims, s_pairs, so);
         if (alive) ++c_flights;
         c_att += so.attempts;
         if (res == kStepLanded) {
@@ -816,7 +822,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                 }
                 if (P.energy) atomicAdd(P.energy + ci, (double)E);
                 if (P.score) atomicAdd(P.score + ci, (double)S.score);
-                if (kScoreT) atomicAdd(P.score_T + ci, (double)S.scoreT);
+                if (kMode == kModeScoreT) atomicAdd(P.score_T + ci, (double)S.scoreT);
                 if (P.hist_E) {
                     int b = min(max((int)(E * P.ebin_per_eV), 0), P.n_ebins - 1);
                     atomicAdd(reinterpret_cast<unsigned long long*>(P.hist_E) + (size_t)S.inst * P.n_ebins + b, 1ull);
@@ -929,7 +935,9 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         for (int r = 1; r < kTraceRows; ++r) {
             if (!__any_sync(kFull, running)) break;
             StepOut so;
-            const int status = flight_step_warp<false>(running, S, P, T, P.prims, P.pairs, so);
+            const int status = P.E_switch > 0.0f
+                                   ? flight_step_warp<kModeWalk>(running, S, P, T, P.prims, P.pairs, so)
+                                   : flight_step_warp<kModePlain>(running, S, P, T, P.prims, P.pairs, so);
             if (running) {
                 double* q = o + (size_t)r * 10;
                 float px = S.px, py = S.py, pz = S.pz;
@@ -978,26 +986,35 @@ size_t transport_smem_bytes(const Params& p) { return smem_layout(p).total; }
 
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem)
 {
-    // the smaller occupancy of the instances with and without the temperature score
-    int nb = 0, nt = 0;
-    cudaError_t e, e2;
+    // the smallest occupancy of the three instances of this count type
+    int nb[3] = {0, 0, 0};
+    cudaError_t e[3];
     if (count64) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<true, false>, threads, smem);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, transport_kernel<true, true>, threads, smem);
+        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], transport_kernel<true, kModePlain>, threads, smem);
+        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], transport_kernel<true, kModeScoreT>, threads, smem);
+        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], transport_kernel<true, kModeWalk>, threads, smem);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transport_kernel<false, false>, threads, smem);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, transport_kernel<false, true>, threads, smem);
+        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], transport_kernel<false, kModePlain>, threads, smem);
+        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], transport_kernel<false, kModeScoreT>, threads, smem);
+        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], transport_kernel<false, kModeWalk>, threads, smem);
     }
-    return (e == cudaSuccess && e2 == cudaSuccess) ? (nb < nt ? nb : nt) : 0;
+    int m = nb[0];
+    for (int i = 0; i < 3; ++i) {
+        if (e[i] != cudaSuccess) return 0;
+        m = nb[i] < m ? nb[i] : m;
+    }
+    return m;
 }
 
 int transport_configure(int max_dynamic_smem)
 {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(transport_kernel<true, false>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, false>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<true, true>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, true>, a, max_dynamic_smem);
+    cudaError_t e = cudaFuncSetAttribute(transport_kernel<true, kModePlain>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, kModePlain>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<true, kModeScoreT>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, kModeScoreT>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<true, kModeWalk>, a, max_dynamic_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, kModeWalk>, a, max_dynamic_smem);
     return (int)e;
 }
 
@@ -1005,11 +1022,14 @@ int transport_launch(const Params& p, int count64, int blocks, int threads, size
 {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (p.score_T) {
-        if (count64) transport_kernel<true, true><<<blocks, threads, smem, s>>>(p);
-        else transport_kernel<false, true><<<blocks, threads, smem, s>>>(p);
+        if (count64) transport_kernel<true, kModeScoreT><<<blocks, threads, smem, s>>>(p);
+        else transport_kernel<false, kModeScoreT><<<blocks, threads, smem, s>>>(p);
+    } else if (p.E_switch > 0.0f) {
+        if (count64) transport_kernel<true, kModeWalk><<<blocks, threads, smem, s>>>(p);
+        else transport_kernel<false, kModeWalk><<<blocks, threads, smem, s>>>(p);
     } else {
-        if (count64) transport_kernel<true, false><<<blocks, threads, smem, s>>>(p);
-        else transport_kernel<false, false><<<blocks, threads, smem, s>>>(p);
+        if (count64) transport_kernel<true, kModePlain><<<blocks, threads, smem, s>>>(p);
+        else transport_kernel<false, kModePlain><<<blocks, threads, smem, s>>>(p);
     }
     return (int)cudaGetLastError();
 }
