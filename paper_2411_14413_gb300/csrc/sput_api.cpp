@@ -95,6 +95,7 @@ struct sput_scene {
     std::vector<DevInstance> dinst;
     std::vector<unsigned long long> prefix;
     std::vector<float4> wtab;
+    int n_w_smem = 0;  // leading entries of wtab staged in shared memory (K and M tables)
     std::vector<float4> rt;
     std::vector<std::vector<double>> lt_weights;  // copies of the cathodes' joint launch tables
     std::vector<float> lt;                        // their CDFs (DevCathode::lt_off)
@@ -398,6 +399,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->dpairs.resize(S->pair_phys.size());
     S->pair_monotone.resize(S->pair_phys.size());
     const double h_w = 0.02;
+    std::vector<std::vector<float4>> g_tabs(S->pair_phys.size());
     for (size_t p = 0; p < S->pair_phys.size(); ++p) {
         const PairPhys& pp = S->pair_phys[p];
         double v_top = std::sqrt(2.0 * S->pair_E_top[p] / (pp.m1 * kEnergyUnit)) + 12.0 * S->s_gas;
@@ -415,14 +417,20 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         S->wtab.insert(S->wtab.end(), K.begin(), K.end());
         D.M_off = (int)S->wtab.size();
         S->wtab.insert(S->wtab.end(), M.begin(), M.end());
-        D.G_off = (int)S->wtab.size();
-        S->wtab.insert(S->wtab.end(), Gt.begin(), Gt.end());
+        g_tabs[p] = std::move(Gt);
         D.sigma_D = S->physics.thermal_switch_eV > 0.0 ? (float)sigma_D64(pp, S->bt, S->chamber.gas_T) : 0.0f;
         D.pad_d[0] = D.pad_d[1] = D.pad_d[2] = 0.0f;
         D.n_w = n_w;
         D.w_inv_h = (float)(1.0 / h_w);
         D.inv_s = (float)(1.0 / S->s_gas);
         S->pair_monotone[p] = h_monotone(pp, S->bt, v_top + 20.0 * S->s_gas);
+    }
+    // the d ln K/d ln s tables follow every K and M table: only K and M are staged in
+    // shared memory; the temperature-score instance reads these from global memory
+    S->n_w_smem = (int)S->wtab.size();
+    for (size_t p = 0; p < S->pair_phys.size(); ++p) {
+        S->dpairs[p].G_off = (int)S->wtab.size();
+        S->wtab.insert(S->wtab.end(), g_tabs[p].begin(), g_tabs[p].end());
     }
 
     // cathodes
@@ -580,7 +588,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.n_pairs = (int)S->dpairs.size();
     p.n_inst = (int)S->dinst.size();
     p.n_bm = (int)bm.size();
-    p.n_w_total = (int)S->wtab.size();
+    p.n_w_total = S->n_w_smem;
     p.bm_lo = bt ? (float)bt->lo : 0.0f;
     p.bm_inv_h = bt ? (float)(1.0 / bt->h) : 1.0f;
     for (int a = 0; a < 3; ++a) {

@@ -114,11 +114,11 @@ struct Params {
     const unsigned long long* prefix;  // n_inst + 1 ticket offsets
     const float4* bm_tab;              // n_bm cubic pieces of b_max/a over ln eps
     const float* xh_tab;               // n_bm + 1 head-on apsis values (linear)
-    const float4* w_tab;               // all pairs' K and M pieces
+    const float4* w_tab;               // all pairs' K and M pieces, then their d ln K/d ln s pieces
     const float4* rt_tab;              // racetrack inverse-CDF pieces (2 rt_n per cathode)
     const float* lt_tab;               // joint launch-table CDFs (see DevCathode::lt_off)
     int n_prims, n_geoms, n_pairs, n_inst;
-    int n_bm, n_w_total;
+    int n_bm, n_w_total;               // n_w_total: leading w_tab entries (K, M) staged in shared memory
     float bm_lo, bm_inv_h;
     float box_lo[3], box_hi[3];
     float s_gas;

@@ -408,7 +408,8 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     // temperature score: d ln(n_g K(v)/v)/dT = (-1 + G/2)/T with n_g = p/(k_B T), G = d ln K/d ln s
     float aT = 0.0f;
     if (kScoreT) {
-        out.Gv = wtab_eval(T, pr, pr.G_off, S.speed);
+        // (this table stays in global memory: w_tab + G_off, read through L1)
+        out.Gv = cubic_eval(P.w_tab + pr.G_off, pr.n_w, log1pf(S.speed * pr.inv_s) * pr.w_inv_h);
         aT = (0.5f * out.Gv - 1.0f) * P.inv_T;
     }
 
