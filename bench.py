@@ -52,10 +52,10 @@ WORKLOAD = WORKLOADS["quaternary"]
 # measures speed against one definition of the work.
 LANE_OPS_PER_COLLISION = 4136.0
 # DRAM bytes (read + write) of one launch of the quaternary workload, from the
-# one-pass capture of the current kernel (mean of 5 launches: 3.22 MB read,
+# one-pass capture of the current kernel (mean of 5 launches: 3.11 MB read,
 # 0 written; the tallies stay in L2); None whenever the kernel changed after
 # the capture.
-TRAFFIC_PER_LAUNCH = 3.22e6
+TRAFFIC_PER_LAUNCH = 3.11e6
 LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes issue one instruction per clock each
 
 
