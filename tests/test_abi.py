@@ -105,6 +105,8 @@ def _create(scene):
     (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.ones((4, 4)), "E_hi": 0.0}), 2),
     (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.ones((300, 4)), "E_hi": 100.0}), 2),
     (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.full((4, 4), np.nan), "E_hi": 100.0}), 2),
+    (lambda s: s.physics.__setitem__("thermal_switch_eV", -1.0), 2),
+    (lambda s: s.physics.update({"thermal_switch_eV": 0.1, "gas_motion": "stationary"}), 2),
 ])
 def test_host_validation_rejects_bad_scenes(lib, mutate, expect):
     """Invalid descriptions fail in host validation, before any CUDA call."""
