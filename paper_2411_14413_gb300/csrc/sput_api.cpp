@@ -306,11 +306,12 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     DeviceGuard guard(device);
     if (!guard.ok) return fail(SPUT_ERR_CUDA, "cudaSetDevice failed");
 
+    int n_sm = 0, optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device));
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     sput_scene* S = new sput_scene();
     S->device = device;
-    CUDA_TRY(cudaDeviceGetAttribute(&S->n_sm, cudaDevAttrMultiProcessorCount, device));
-    int optin = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    S->n_sm = n_sm;
     S->smem_optin = (size_t)optin;
     S->chamber = desc->chamber;
     S->grid = desc->grid;
