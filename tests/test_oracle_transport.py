@@ -219,3 +219,28 @@ def test_collision_cap_counts_timed_out(oracle_mod):
     t = oracle_mod.tally(sc, out)
     assert t["timed_out"][0] > 0
     assert t["prim_counts"].sum() + t["timed_out"].sum() == 300
+
+
+def test_trace_agrees_with_the_outcome(oracle_mod):
+    """The per-flight trace (used for GPU trace parity) ends where the particle's
+    outcome says: the landing primitive, the collision count, the arrival energy,
+    and a path whose collided flights join end to start."""
+    sc = workloads.scene_single_ni(n=40)
+    osc = oracle_mod.OracleScene(sc)
+    out = osc.run_all()
+    m_ni = sc.cathodes[0]["element"].mass
+    for pid in range(40):
+        tr = osc.trace(0, pid, rows=4096)
+        status = tr[:, 7]
+        last = int(np.nonzero(status >= 0)[0].max())
+        if out["prim"][pid] >= 0:
+            assert status[last] == 1 and int(tr[last, 8]) == out["prim"][pid]
+        else:
+            assert status[last] == 2
+        assert np.sum(status[1:last] == 0) == out["ncoll"][pid]
+        E = 0.5 * m_ni * tr[last, 6] ** 2 * oracle_mod.c_energy()
+        assert abs(E - out["E"][pid]) < 1e-9 * out["E"][pid]
+        for r in range(1, last):
+            # row r holds the collision point of flight r: row r-1 position + t * direction of row r-1
+            step = tr[r - 1, :3] + tr[r, 9] * tr[r - 1, 3:6]
+            assert np.allclose(step, tr[r, :3], atol=1e-9 * (1 + np.abs(step).max()))
