@@ -92,7 +92,7 @@ typedef enum sput_interaction {
 } sput_interaction;
 
 typedef enum sput_gas_motion {
-    SPUT_GAS_THERMAL = 0,    /* Maxwellian gas at T (paper: gas motion taken into account) */
+    SPUT_GAS_THERMAL = 0,    /* Maxwellian gas at T (the paper accounts for the motion of the gas) */
     SPUT_GAS_STATIONARY = 1  /* gas atoms at rest (test mode) */
 } sput_gas_motion;
 
@@ -312,9 +312,10 @@ sput_status sput_run_host(sput_scene* scene, const sput_run_opts* opts, const sp
  * GPU that loads the library holds until the process exits.  It never calls
  * cudaMalloc, cudaFree or any other allocating routine; the scene (inputs) and
  * the tallies (outputs) are passed in exactly as for sput_run.
- *   - The first call on a device looks up the array's device address with that
- *     device current and caches it; make that first call before any stream
- *     capture.
+ *   - The first call in a CUDA context of a device looks up the array's device
+ *     address with that device current and caches it under the context's id
+ *     (a context created again after cudaDeviceReset looks it up afresh); make
+ *     that first call before any stream capture.
  *   - All calls on one device share the array and it keeps the last call's
  *     contents; each call clears the counters it needs before its kernel.
  *     Calls whose work overlaps on the GPU (other streams, other threads,
@@ -322,7 +323,9 @@ sput_status sput_run_host(sput_scene* scene, const sput_run_opts* opts, const sp
  *   - A run whose scratch would exceed the array's capacity is rejected with
  *     SPUT_ERR_UNSUPPORTED and a message naming both sizes.
  *   - With stats != NULL the call waits for the stream (opts->timeout_ms
- *     applies) and also reuses the scene's pinned statistics buffer.
+ *     applies) and also reuses the scene's pinned statistics buffer and its two
+ *     timing events for kernel_ms; a run of the same scene that overlaps this
+ *     one overwrites them, which is one more reason to serialise such calls.
  * The paper has no counterpart of this entry point. */
 sput_status sput_run_noalloc(sput_scene* scene, const sput_run_opts* opts, void* stream, const sput_tallies* tallies,
                              sput_run_stats* stats);

@@ -714,7 +714,8 @@ sput_status ensure_scratch(sput_scene* S)
 }
 
 sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stream, const sput_tallies* T,
-                     sput_run_stats* stats, unsigned long long* scratch)
+                     sput_run_stats* stats, unsigned long long* scratch, int* blocks_out = nullptr,
+                     int* threads_out = nullptr)
 {
     if (!opts || !T) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     if (T->hist_E && S->grid.n_ebins == 0) return fail(SPUT_ERR_INVALID_ARG, "hist_E requested but n_ebins = 0");
@@ -779,6 +780,8 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     unsigned long long need = (te - tb + threads - 1) / threads;
     int blocks = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>((unsigned long long)S->n_sm * bps, need));
     if (te == tb) blocks = 1;
+    if (blocks_out) *blocks_out = blocks;
+    if (threads_out) *threads_out = threads;
     CUDA_TRY(cudaEventRecord(S->ev0, stream));
     int le = transport_launch(p, c64, blocks, threads, smem, stream);
     if (le != 0) return cuda_fail((cudaError_t)le, "transport kernel launch");
@@ -906,7 +909,8 @@ sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* str
     int e0 = static_scratch_address(S->device, &scratch);
     if (e0 != 0) return cuda_fail((cudaError_t)e0, "cudaGetSymbolAddress(static run scratch)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    sput_status rs = run_impl(S, opts, st, T, nullptr, scratch);
+    int blocks = 0, threads = 0;
+    sput_status rs = run_impl(S, opts, st, T, nullptr, scratch, &blocks, &threads);
     if (rs != SPUT_OK || !stats) return rs;
     CUDA_TRY(cudaMemcpyAsync(S->h_scratch, scratch, kRunScratchBytes, cudaMemcpyDeviceToHost, st));
     auto t0 = std::chrono::steady_clock::now();
@@ -928,10 +932,13 @@ sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* str
     stats->collisions = h[5];
     stats->attempts = h[6];
     stats->device_status = (uint32_t)(h[1 + kNumStats] & 0xffffffffu);
-    stats->grid_blocks = 0;
-    stats->block_threads = (uint32_t)(opts->block_threads ? opts->block_threads : S->def_threads);
+    stats->grid_blocks = (uint32_t)blocks;
+    stats->block_threads = (uint32_t)threads;
+    // the kernel time comes from the scene's two timing events, which every run of
+    // the scene records: a run of the same scene that overlaps this one overwrites
+    // them (the same race as on the scratch array)
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+    CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
     stats->kernel_ms = ms;
     if (stats->device_status) return fail(SPUT_ERR_DEVICE_CHECK, "device status bits set");
     return SPUT_OK;

@@ -181,7 +181,8 @@ void set_last_error(const char* msg);
 constexpr size_t kRunScratchBytes = 64;      // ticket counter + kNumStats statistics + status word
 constexpr size_t kStaticScratchBytes = 256;  // capacity of the static array
 // Device address of the static scratch for `device` (must be current); looked
-// up with cudaGetSymbolAddress on the first call per device, then cached.
+// up with cudaGetSymbolAddress on the first call in each CUDA context of the
+// device, then cached under the context's id (a reset device gets a new one).
 int static_scratch_address(int device, unsigned long long** out);
 
 }  // namespace sput

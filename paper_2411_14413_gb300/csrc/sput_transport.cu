@@ -9,12 +9,14 @@
 // scattering angle is computed from the classical deflection integral by
 // Gauss-Mehler quadrature in FP32.  Counts are integer atomics (bit-exact,
 // order independent); energy and score sums are FP64 atomics.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "sput_internal.h"
 
@@ -1047,16 +1049,51 @@ int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev,
 // in module memory, so that a run needs no device allocation at all.  Every
 // device that loads the library holds these kStaticScratchBytes until the
 // process exits.  In host code the name below is only a stand-in for the
-// device symbol; its device address is looked up per device, with that
-// device current, and cached.
+// device symbol; its device address is looked up with the device current.
 static __device__ __align__(256) unsigned long long g_static_run_scratch[kStaticScratchBytes / 8];
+
+namespace {
+// The address is cached per CUDA context, identified by the driver's context
+// id: a context torn down and created again (cudaDeviceReset) gets a new id,
+// so a stale address is never reused.  The two driver entry points are taken
+// through the runtime, which needs no link against the driver library.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+int current_context_id(unsigned long long* id)
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return (int)e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return (int)cudaErrorNotSupported;
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(f0);
+        get_id = reinterpret_cast<PfnCtxGetId>(f1);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return (int)cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return (int)cudaErrorDeviceUninitialized;
+    return 0;
+}
+}  // namespace
 
 int static_scratch_address(int device, unsigned long long** out)
 {
     static std::mutex mu;
-    static std::map<int, unsigned long long*> cache;
+    static std::map<std::pair<int, unsigned long long>, unsigned long long*> cache;
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(device);
+    unsigned long long ctx_id = 0;
+    int e0 = current_context_id(&ctx_id);
+    if (e0 != 0) return e0;
+    const auto key = std::make_pair(device, ctx_id);
+    auto it = cache.find(key);
     if (it != cache.end()) {
         *out = it->second;
         return 0;
@@ -1064,8 +1101,8 @@ int static_scratch_address(int device, unsigned long long** out)
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_run_scratch);
     if (e != cudaSuccess) return (int)e;
-    cache[device] = reinterpret_cast<unsigned long long*>(ptr);
-    *out = cache[device];
+    cache[key] = reinterpret_cast<unsigned long long*>(ptr);
+    *out = cache[key];
     return 0;
 }
 
