@@ -27,6 +27,10 @@ Parity status of each oracle function (pins in tests/test_oracle_*.py):
                            uniform energy loss
   partner weighting        pinned: thermalisation to the collision-weighted
                            Maxwellian
+  pressure score (LR)      pinned: d/d ln p of the uncollided fraction,
+                           -2 kappa E_2(kappa) (closed form); central
+                           finite differences of the landing fractions with
+                           common random numbers
   absolute deposition profile under the chi_min cut-off: parity unpinned
   (no printed value in the paper checks it).
 """
