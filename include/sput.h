@@ -405,6 +405,29 @@ sput_status sput_composition(int n_cathodes, int n_cells, int n_points, const in
 sput_status sput_emax_backward(const sput_scene* scene, const double* grad_counts, const void* counts,
                                const void* counts_cutoff, double* grad_ion_energy, void* stream);
 
+/* Incident ion energy from the cathode power through the discharge voltage.  Table S1
+ * gives the discharge voltage (DC) or bias (RF) of every element and supply at two
+ * powers; the voltage is read as the line through them, and singly charged ions give
+ * E_i = e V (so E_i in eV equals V in volts):
+ *   ion_energy[j] = V_a + (V_b - V_a) (power[j] - P_a) / (P_b - P_a),
+ * voltage HOST double [n][4] = (P_a, V_a, P_b, V_b) per cathode (W, V), power HOST [n] (W),
+ * ion_energy HOST [n] (eV, output; feed it to sput_instances_set).  1 <= n <= 4096; the
+ * two points of a line must be finite with P_a != P_b, else SPUT_ERR_INVALID_ARG.
+ * Host only, synchronous, touches no device. */
+sput_status sput_ion_energy(int n, const double* voltage, const double* power, double* ion_energy);
+
+/* The power's path through the discharge voltage to the Thompson cut-off, in one call:
+ * the sput_emax_backward contraction per instance, grad_ion_energy[i] = dL/dE_i (DEVICE
+ * double [n_instances], written), and then
+ *   grad_power[i] += grad_ion_energy[i] * dE_i/dP_i,   dE_i/dP_i = (V_b - V_a)/(P_b - P_a)
+ * (DEVICE double [n_instances], accumulated into, e.g. after sput_composition_backward has
+ * written the rate-line term).  voltage HOST [n_instances][4] as for sput_ion_energy;
+ * counts / counts_cutoff / grad_counts as for sput_emax_backward.  At most 16 instances
+ * (one per cathode of a composition map).  Asynchronous on `stream`. */
+sput_status sput_voltage_backward(const sput_scene* scene, const double* voltage, const double* grad_counts,
+                                  const void* counts, const void* counts_cutoff, double* grad_ion_energy,
+                                  double* grad_power, void* stream);
+
 /* Backward pass of sput_composition: from grad_composition (DEVICE [n_points][n_cathodes])
  * and the forward's patch_counts, writes grad_patch (DEVICE [n_cathodes][n_points], scratch
  * owned by the caller), grad_counts (DEVICE double [n_cathodes][n_cells]) and grad_power

@@ -205,6 +205,8 @@ SIGNATURES = {
     "sput_graph_destroy": (None, [_P]),
     "sput_backward": (C.c_int, [_P, _P, _P, _P, _P]),
     "sput_emax_backward": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "sput_ion_energy": (C.c_int, [C.c_int, _P, _P, _P]),
+    "sput_voltage_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "sput_composition": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P]),
     "sput_composition_backward": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
                                             _P]),

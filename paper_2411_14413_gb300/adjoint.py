@@ -5,7 +5,9 @@ forward = transport with score tallies (sput_run) followed by the
 counts -> at.% map (sput_composition); backward = the composition map's
 backward pass (sput_composition_backward, which also gives dL/dP through the
 rate lines) followed by the likelihood-ratio contraction for the pressure
-(sput_backward).  Python only marshals pointers.
+(sput_backward) and, with voltage lines, the power's path through the
+discharge voltage to the Thompson cut-off (sput_voltage_backward).  Python
+only marshals pointers.
 
 ``inverse_solve`` fits (ln p, P_1..P_n) to a target composition map with
 Adam, using common random numbers (a fixed seed) in every step.
@@ -33,7 +35,9 @@ class MapSetup:
     voltage of each cathode as the line through two (power, voltage) points
     (Table S1); the incident ion energy E_i (eV, singly charged ions) then
     follows the power, which moves the Thompson cut-off E_max = k Lambda E_i - U_s,
-    and backward() adds that path to dL/dP (boundary run + sput_emax_backward)."""
+    and backward() adds that path to dL/dP (boundary run + sput_voltage_backward).
+    The voltage arithmetic itself runs in the library (sput_ion_energy and
+    sput_voltage_backward); this class only marshals."""
 
     def __init__(self, scene, patch_of_cell, ref_point, calibration, device=0, voltage=None):
         import torch
@@ -62,8 +66,6 @@ class MapSetup:
             self._cut_tal = N.sput_tallies()
             self._cut_tal.counts = self.counts_cut.data_ptr()
             self.grad_Ei = torch.zeros(self.n_cath, dtype=torch.float64, device=dev)
-            self.dV_dP = torch.as_tensor((self.volt[:, 3] - self.volt[:, 1]) / (self.volt[:, 2] - self.volt[:, 0]),
-                                         dtype=torch.float64, device=dev)
 
     def stream(self):
         import torch
@@ -71,9 +73,13 @@ class MapSetup:
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def ion_energy(self, power):
-        """E_i (eV) of every cathode at the given powers, from the voltage lines."""
-        v = self.volt
-        return v[:, 1] + (v[:, 3] - v[:, 1]) * (np.asarray(power, float) - v[:, 0]) / (v[:, 2] - v[:, 0])
+        """E_i (eV) of every cathode at the given powers, from the voltage lines (sput_ion_energy)."""
+        pw = np.ascontiguousarray(power, dtype=np.float64)
+        out = np.empty(self.n_cath, dtype=np.float64)
+        rc = N.load().sput_ion_energy(self.n_cath, self.volt.ctypes.data_as(C.c_void_p), pw.ctypes.data_as(C.c_void_p),
+                                      out.ctypes.data_as(C.c_void_p))
+        N.check(rc, "sput_ion_energy")
+        return out
 
     def set_conditions(self, p, power=None):
         sc = self.scene.with_pressure(float(p))
@@ -115,10 +121,11 @@ class MapSetup:
             # the same particles launched at E_max: the moving end of the Thompson support
             o = api.run_opts(seed=self.seed, flags=N.SPUT_RUN_LAUNCH_AT_CUTOFF)
             api.sput_run(self.tr.h, o, self.stream(), self._cut_tal, False)
-            rc = L.sput_emax_backward(self.tr.h, _ptr(self.grad_counts), _ptr(self.tr.t["counts"]),
-                                      _ptr(self.counts_cut), _ptr(self.grad_Ei), C.c_void_p(self.stream()))
-            N.check(rc, "sput_emax_backward")
-            self.grad_power.add_(self.grad_Ei * self.dV_dP)
+            # dL/dE_i, and dL/dE_i dE_i/dP added to the rate-line term of dL/dP
+            rc = L.sput_voltage_backward(self.tr.h, self.volt.ctypes.data_as(C.c_void_p), _ptr(self.grad_counts),
+                                         _ptr(self.tr.t["counts"]), _ptr(self.counts_cut), _ptr(self.grad_Ei),
+                                         _ptr(self.grad_power), C.c_void_p(self.stream()))
+            N.check(rc, "sput_voltage_backward")
         return self.grad_logp, self.grad_power
 
     def close(self):

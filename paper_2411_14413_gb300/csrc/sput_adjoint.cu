@@ -16,6 +16,7 @@
 // central patch, R_j linear in power through two calibration points.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -65,9 +66,18 @@ __global__ void lr_backward_kernel(const double* g, const double* score, double*
 // With a boundary run of the same particles launched at E_max (counts_cut) and
 // dE_max/dE_i = k Lambda, one block per instance forms
 //   grad[i] = k Lambda p(E_max) sum_c g[i][c] (counts_cut[i][c] - counts[i][c]).
+// Voltage lines V_i(P) = V_a + (V_b - V_a)(P - P_a)/(P_b - P_a) (Table S1), with
+// E_i = e V for singly charged ions: dE_i/dP_i in eV/W per instance.
+struct VoltParams {
+    double dEdP[kMaxCath];
+};
+
+// grad_power (optional) gets grad[i] * dE_i/dP_i added: the path from the cathode
+// power through the discharge voltage to the cut-off.
 template <typename CountT>
 __global__ void emax_backward_kernel(const double* g, const CountT* counts, const CountT* counts_cut,
-                                     const sput::DevInstance* inst, double* grad, long long n_cells)
+                                     const sput::DevInstance* inst, double* grad, long long n_cells,
+                                     double* grad_power, VoltParams vp)
 {
     __shared__ double part[32];
     const long long base = (long long)blockIdx.x * n_cells;
@@ -84,7 +94,9 @@ __global__ void emax_backward_kernel(const double* g, const CountT* counts, cons
             const sput::DevInstance I = inst[blockIdx.x];
             const double q = I.thompson_q, U = I.U_s;
             const double Em = U * q / (1.0 - q);
-            grad[blockIdx.x] = (double)I.kLambda * 2.0 * U / (Em * (Em + U)) * t;
+            const double gE = (double)I.kLambda * 2.0 * U / (Em * (Em + U)) * t;
+            grad[blockIdx.x] = gE;
+            if (grad_power) grad_power[blockIdx.x] += gE * vp.dEdP[blockIdx.x];
         }
     }
 }
@@ -214,28 +226,93 @@ sput_status sput_backward(const sput_scene* scene, const double* grad_counts, co
     return SPUT_OK;
 }
 
-sput_status sput_emax_backward(const sput_scene* scene, const double* grad_counts, const void* counts,
-                               const void* counts_cutoff, double* grad_ion_energy, void* stream)
+}  // extern "C"
+
+namespace {
+
+sput_status emax_backward_launch(const sput_scene* scene, const double* grad_counts, const void* counts,
+                                 const void* counts_cutoff, double* grad_ion_energy, double* grad_power,
+                                 const VoltParams& vp, void* stream)
 {
-    if (!scene || !grad_counts || !counts || !counts_cutoff || !grad_ion_energy)
-        return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     sput_tally_layout L;
     sput_status st = sput_tally_layout_get(scene, &L);
     if (st != SPUT_OK) return st;
+    if (grad_power && L.n_instances > kMaxCath)
+        return adj_fail(SPUT_ERR_INVALID_ARG, "the voltage path supports at most 16 instances");
     const long long n_cells = (long long)L.nx * L.ny;
     const sput::DevInstance* inst = sput::scene_device_instances(scene);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (L.count_type == SPUT_COUNT_INT64)
         emax_backward_kernel<<<L.n_instances, 256, 0, s>>>(grad_counts, static_cast<const long long*>(counts),
                                                            static_cast<const long long*>(counts_cutoff), inst,
-                                                           grad_ion_energy, n_cells);
+                                                           grad_ion_energy, n_cells, grad_power, vp);
     else
         emax_backward_kernel<<<L.n_instances, 256, 0, s>>>(grad_counts, static_cast<const int*>(counts),
                                                            static_cast<const int*>(counts_cutoff), inst,
-                                                           grad_ion_energy, n_cells);
+                                                           grad_ion_energy, n_cells, grad_power, vp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return adj_fail(SPUT_ERR_CUDA, cudaGetErrorString(e));
     return SPUT_OK;
+}
+
+// slope dV/dP of each voltage line (P_a, V_a, P_b, V_b); E_i = e V, so dE_i/dP in eV/W
+sput_status voltage_slopes(int n, const double* voltage, double* slope)
+{
+    if (n < 1 || !voltage) return adj_fail(SPUT_ERR_INVALID_ARG, "NULL voltage lines or no instance");
+    for (int j = 0; j < n; ++j) {
+        const double* q = voltage + 4 * j;
+        if (!(q[2] != q[0]) || !std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) ||
+            !std::isfinite(q[3]))
+            return adj_fail(SPUT_ERR_INVALID_ARG, "voltage line needs two finite points at distinct powers");
+        slope[j] = (q[3] - q[1]) / (q[2] - q[0]);
+    }
+    return SPUT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sput_status sput_emax_backward(const sput_scene* scene, const double* grad_counts, const void* counts,
+                               const void* counts_cutoff, double* grad_ion_energy, void* stream)
+{
+    if (!scene || !grad_counts || !counts || !counts_cutoff || !grad_ion_energy)
+        return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    VoltParams vp;
+    std::memset(&vp, 0, sizeof vp);
+    return emax_backward_launch(scene, grad_counts, counts, counts_cutoff, grad_ion_energy, nullptr, vp, stream);
+}
+
+sput_status sput_ion_energy(int n, const double* voltage, const double* power, double* ion_energy)
+{
+    if (!power || !ion_energy) return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    if (n > 4096) return adj_fail(SPUT_ERR_INVALID_ARG, "at most 4096 lines");
+    for (int j = 0; j < n; ++j) {
+        double slope;
+        sput_status st = voltage_slopes(1, voltage + 4 * j, &slope);
+        if (st != SPUT_OK) return st;
+        if (!std::isfinite(power[j])) return adj_fail(SPUT_ERR_INVALID_ARG, "power must be finite");
+        const double* q = voltage + 4 * j;
+        ion_energy[j] = q[1] + slope * (power[j] - q[0]);  // singly charged ions: eV = e * volts
+    }
+    return n >= 1 ? SPUT_OK : adj_fail(SPUT_ERR_INVALID_ARG, "no voltage line");
+}
+
+sput_status sput_voltage_backward(const sput_scene* scene, const double* voltage, const double* grad_counts,
+                                  const void* counts, const void* counts_cutoff, double* grad_ion_energy,
+                                  double* grad_power, void* stream)
+{
+    if (!scene || !grad_counts || !counts || !counts_cutoff || !grad_ion_energy || !grad_power)
+        return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
+    sput_tally_layout L;
+    sput_status st = sput_tally_layout_get(scene, &L);
+    if (st != SPUT_OK) return st;
+    if (L.n_instances > kMaxCath) return adj_fail(SPUT_ERR_INVALID_ARG, "the voltage path supports at most 16 instances");
+    VoltParams vp;
+    std::memset(&vp, 0, sizeof vp);
+    st = voltage_slopes(L.n_instances, voltage, vp.dEdP);
+    if (st != SPUT_OK) return st;
+    return emax_backward_launch(scene, grad_counts, counts, counts_cutoff, grad_ion_energy, grad_power, vp, stream);
 }
 
 sput_status sput_composition(int n_cathodes, int n_cells, int n_points, const int64_t* counts, const int32_t* patch_of_cell,

@@ -122,3 +122,29 @@ def test_null_arguments(lib):
     assert lib.sput_run(None, None, None, None, None) == 1
     assert lib.sput_probe(None, 0, 0, 1, None, None) == 1
     lib.sput_scene_destroy(None)
+
+
+def test_ion_energy_from_table_s1_voltage_lines(lib):
+    """sput_ion_energy (host only): at the two Table S1 powers of each element's supply
+    the ion energy equals the tabulated voltage (singly charged ions: E_i/eV = V/volt),
+    midway it is their mean, and the line extrapolates; bad lines are rejected."""
+    from workloads.measurement import voltage_points
+
+    syms = ("Ni", "Pd", "Pt", "Ru")
+    volt = np.array([[*voltage_points(s)[0], *voltage_points(s)[1]] for s in syms], dtype=np.float64)
+    out = np.zeros(4)
+    for col_p, col_v in ((0, 1), (2, 3)):
+        pw = np.ascontiguousarray(volt[:, col_p])
+        assert lib.sput_ion_energy(4, volt.ctypes.data, pw.ctypes.data, out.ctypes.data) == 0
+        assert np.array_equal(out, volt[:, col_v])
+    pw = np.ascontiguousarray(0.5 * (volt[:, 0] + volt[:, 2]))
+    assert lib.sput_ion_energy(4, volt.ctypes.data, pw.ctypes.data, out.ctypes.data) == 0
+    assert np.allclose(out, 0.5 * (volt[:, 1] + volt[:, 3]), rtol=1e-14)
+    pw = np.ascontiguousarray(2 * volt[:, 2] - volt[:, 0])  # one line length beyond P_b
+    assert lib.sput_ion_energy(4, volt.ctypes.data, pw.ctypes.data, out.ctypes.data) == 0
+    assert np.allclose(out, 2 * volt[:, 3] - volt[:, 1], rtol=1e-13)
+    bad = volt.copy()
+    bad[1, 2] = bad[1, 0]
+    assert lib.sput_ion_energy(4, bad.ctypes.data, pw.ctypes.data, out.ctypes.data) == 1
+    assert lib.sput_ion_energy(0, volt.ctypes.data, pw.ctypes.data, out.ctypes.data) == 1
+    assert lib.sput_ion_energy(4, None, pw.ctypes.data, out.ctypes.data) == 1
