@@ -437,6 +437,43 @@ sput_status sput_composition_backward(int n_cathodes, int n_cells, int n_points,
                                       const double* power, const double* grad_composition, double* grad_patch,
                                       double* grad_counts, double* grad_power, void* stream);
 
+/* Measured throughput of the units the transport kernel issues to, for its roofline
+ * (no counterpart in the paper; measurement only).  One kernel per call, launched with
+ * SMs x 8 blocks of 256 threads; a warm-up launch, then one launch timed with CUDA events
+ * on `stream`.  Synchronous.
+ *   SPUT_MB_FFMA      FP32 fused multiply-adds (lane-ops)
+ *   SPUT_MB_MUFU_*    lg2 / ex2 / rsqrt / sin on the MUFU (XU) pipe, approximate forms (lane-ops)
+ *   SPUT_MB_PHILOX    Philox4x32-10 blocks (10 rounds of the generator the transport uses)
+ *   SPUT_MB_RED_*     L2 reductions (atomic adds whose result is unused, as in the landing
+ *                     tally) of int32 / int64 / fp64 at pseudo-random slots of an array of
+ *                     n_slots elements
+ * scratch: DEVICE buffer owned by the caller; the reductions use its first n_slots
+ * elements (cleared first), the other kinds need room for SMs * 8 * 256 floats (a sink
+ * that is written only under a condition that never holds).  iters in [1, 2^24] sets the
+ * work per thread.  out->ops counts the lane-ops (or blocks, or reductions) of the timed
+ * launch, out->ms its device time. */
+typedef enum sput_microbench_kind {
+    SPUT_MB_FFMA = 0,
+    SPUT_MB_MUFU_LG2 = 1,
+    SPUT_MB_MUFU_EX2 = 2,
+    SPUT_MB_MUFU_RSQ = 3,
+    SPUT_MB_MUFU_SIN = 4,
+    SPUT_MB_PHILOX = 5,
+    SPUT_MB_RED_I32 = 6,
+    SPUT_MB_RED_I64 = 7,
+    SPUT_MB_RED_F64 = 8
+} sput_microbench_kind;
+
+typedef struct sput_microbench_result {
+    double ops;                  /* units of work in the timed launch */
+    double ms;                   /* its device time */
+    double ops_per_s;
+    int blocks, threads;         /* launch shape */
+} sput_microbench_result;
+
+sput_status sput_microbench(int device, int kind, int n_slots, void* scratch, size_t scratch_bytes, int iters,
+                            void* stream, sput_microbench_result* out);
+
 /* Free the scene and its device memory. */
 void sput_scene_destroy(sput_scene* scene);
 

@@ -20,7 +20,7 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libsput.so")
-SOURCES = ["sput_api.cpp", "sput_tables.cpp", "sput_transport.cu", "sput_adjoint.cu"]
+SOURCES = ["sput_api.cpp", "sput_tables.cpp", "sput_transport.cu", "sput_adjoint.cu", "sput_microbench.cu"]
 HEADERS = ["sput_internal.h", "sput_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -177,13 +177,21 @@ class sput_tune_result(C.Structure):
                      flags=self.cand_flags[i], rate=self.cand_rate[i]) for i in range(self.n_candidates)]
 
 
+class sput_microbench_result(C.Structure):
+    _fields_ = [("ops", C.c_double), ("ms", C.c_double), ("ops_per_s", C.c_double), ("blocks", C.c_int),
+                ("threads", C.c_int)]
+
+
+MICROBENCH_KINDS = {"ffma": 0, "mufu_lg2": 1, "mufu_ex2": 2, "mufu_rsqrt": 3, "mufu_sin": 4, "philox": 5,
+                    "red_i32": 6, "red_i64": 7, "red_f64": 8}
+
 SPUT_RUN_NO_SMEM_COUNTERS = 1
 SPUT_RUN_SMEM_COUNTERS = 2
 SPUT_RUN_LAUNCH_AT_CUTOFF = 4
 
 ABI_STRUCTS = [sput_chamber, sput_primitive, sput_geometry, sput_cathode, sput_instance, sput_grid, sput_physics,
                sput_scene_desc, sput_record, sput_tallies, sput_tally_layout, sput_run_opts, sput_run_stats,
-               sput_tune_result]
+               sput_tune_result, sput_microbench_result]
 
 # name -> (restype, argtypes) for every entry point declared in include/sput.h
 _P = C.c_void_p
@@ -211,6 +219,8 @@ SIGNATURES = {
     "sput_composition_backward": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
                                             _P]),
     "sput_probe": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "sput_microbench": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.c_size_t, C.c_int, _P,
+                                  C.POINTER(sput_microbench_result)]),
 }
 
 

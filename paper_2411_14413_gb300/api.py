@@ -194,6 +194,16 @@ def sput_graph_destroy(graph):
         _lib().sput_graph_destroy(graph)
 
 
+def sput_microbench(device, kind, scratch, iters, stream, n_slots=0):
+    """Throughput of one unit (see include/sput.h); scratch is a device tensor."""
+    res = N.sput_microbench_result()
+    k = N.MICROBENCH_KINDS[kind] if isinstance(kind, str) else int(kind)
+    rc = _lib().sput_microbench(int(device), k, int(n_slots), C.c_void_p(scratch.data_ptr()),
+                                scratch.numel() * scratch.element_size(), int(iters), C.c_void_p(stream), C.byref(res))
+    N.check(rc, "sput_microbench")
+    return res
+
+
 # ------------------------------------------------------------ convenience
 class Transport:
     """A scene resident on one GPU plus torch-allocated tallies.

@@ -51,7 +51,7 @@ _LAYOUT_C = r"""
 int main(void) {
   S(sput_chamber) S(sput_primitive) S(sput_geometry) S(sput_cathode) S(sput_instance) S(sput_grid)
   S(sput_physics) S(sput_scene_desc) S(sput_record) S(sput_tallies) S(sput_tally_layout) S(sput_run_opts)
-  S(sput_run_stats) S(sput_tune_result)
+  S(sput_run_stats) S(sput_tune_result) S(sput_microbench_result)
   O(sput_tune_result, cand_rate) O(sput_run_opts, flags)
   O(sput_scene_desc, chamber) O(sput_scene_desc, prims) O(sput_scene_desc, grid) O(sput_scene_desc, physics)
   O(sput_cathode, rt_r0) O(sput_cathode, cos_coef) O(sput_cathode, launch_table) O(sput_cathode, n_E)
