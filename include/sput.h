@@ -251,6 +251,9 @@ typedef struct sput_run_opts {
                                        boundary run of the derivative with respect to the Thompson cut-off,
                                        d E[f]/dE_max = p(E_max) (E[f | E = E_max] - E[f]),
                                        p(E_max) = 2 U_s / (E_max (E_max + U_s)); Thompson cathodes only */
+#define SPUT_RUN_INJECT_NONFINITE 8 /* failure-path test aid: particle 0 of every instance starts with a NaN
+                                       speed; the kernel retires it as timed out, sets the non-finite bit of
+                                       device_status and the call returns SPUT_ERR_DEVICE_CHECK (with stats) */
 
 typedef struct sput_run_stats {
     uint64_t particles;          /* particles that completed (landed or timed out) */

@@ -20,6 +20,8 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libsput.so")
+CHECKED_LIB_PATH = os.path.join(BUILD, "libsput_checked.so")
+CHECKED_SOURCE = "sput_transport.cu"
 SOURCES = ["sput_api.cpp", "sput_tables.cpp", "sput_transport.cu", "sput_adjoint.cu", "sput_microbench.cu"]
 HEADERS = ["sput_internal.h", "sput_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,17 +45,21 @@ def _stale(target, deps):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/*.{cpp,cu} for sm_103a (in parallel) and link libsput.so."""
+    """Compile csrc/*.{cpp,cu} for sm_103a (in parallel) and link libsput.so, and
+    libsput_checked.so: the same library with the transport kernel built with
+    SPUT_CHECKED (every table, cell, primitive and record index tested against its
+    buffer, a failure reported in the run's status word)."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "sput.h")]
     common = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 
-    def compile_one(src):
+    def compile_one(job):
+        src, checked = job
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(BUILD, src + (".checked.o" if checked else ".o"))
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc] + common + ["-c", s, "-o", o]
+            cmd = [nvcc] + common + (["-DSPUT_CHECKED"] if checked else []) + ["-c", s, "-o", o]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -61,14 +67,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(r.stdout + r.stderr)
         return o
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    if force or _stale(LIB_PATH, objs):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB_PATH)
+    jobs = [(src, False) for src in SOURCES] + [(CHECKED_SOURCE, True)]
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    regular = objs[:len(SOURCES)]
+    checked = [objs[-1] if SOURCES[i] == CHECKED_SOURCE else regular[i] for i in range(len(SOURCES))]
+    for lib_path, lib_objs in ((LIB_PATH, regular), (CHECKED_LIB_PATH, checked)):
+        if force or _stale(lib_path, lib_objs):
+            tmp = lib_path + f".tmp{os.getpid()}"
+            r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + lib_objs, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+            os.replace(tmp, lib_path)
     return LIB_PATH
 
 
@@ -188,6 +198,7 @@ MICROBENCH_KINDS = {"ffma": 0, "mufu_lg2": 1, "mufu_ex2": 2, "mufu_rsqrt": 3, "m
 SPUT_RUN_NO_SMEM_COUNTERS = 1
 SPUT_RUN_SMEM_COUNTERS = 2
 SPUT_RUN_LAUNCH_AT_CUTOFF = 4
+SPUT_RUN_INJECT_NONFINITE = 8
 
 ABI_STRUCTS = [sput_chamber, sput_primitive, sput_geometry, sput_cathode, sput_instance, sput_grid, sput_physics,
                sput_scene_desc, sput_record, sput_tallies, sput_tally_layout, sput_run_opts, sput_run_stats,

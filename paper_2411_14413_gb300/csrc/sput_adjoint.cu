@@ -214,6 +214,7 @@ extern "C" {
 sput_status sput_backward(const sput_scene* scene, const double* grad_counts, const double* score_tally,
                           double* grad_log_pressure, void* stream)
 {
+    sput::NvtxRange nvtx("sput_backward");
     if (!scene || !grad_counts || !score_tally || !grad_log_pressure) return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     sput_tally_layout L;
     sput_status st = sput_tally_layout_get(scene, &L);
@@ -276,6 +277,7 @@ extern "C" {
 sput_status sput_emax_backward(const sput_scene* scene, const double* grad_counts, const void* counts,
                                const void* counts_cutoff, double* grad_ion_energy, void* stream)
 {
+    sput::NvtxRange nvtx("sput_emax_backward");
     if (!scene || !grad_counts || !counts || !counts_cutoff || !grad_ion_energy)
         return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     VoltParams vp;
@@ -302,6 +304,7 @@ sput_status sput_voltage_backward(const sput_scene* scene, const double* voltage
                                   const void* counts, const void* counts_cutoff, double* grad_ion_energy,
                                   double* grad_power, void* stream)
 {
+    sput::NvtxRange nvtx("sput_voltage_backward");
     if (!scene || !grad_counts || !counts || !counts_cutoff || !grad_ion_energy || !grad_power)
         return adj_fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     sput_tally_layout L;
@@ -339,6 +342,7 @@ sput_status sput_composition_backward(int n_cathodes, int n_cells, int n_points,
                                       const double* power, const double* grad_composition, double* grad_patch,
                                       double* grad_counts, double* grad_power, void* stream)
 {
+    sput::NvtxRange nvtx("sput_composition_backward");
     CompParams cp;
     sput_status st = comp_params(n_cathodes, n_cells, n_points, ref_point, calibration, power, cp);
     if (st != SPUT_OK) return st;

@@ -293,6 +293,7 @@ static sput_status pack_instances(sput_scene* S)
 
 sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scene** out)
 {
+    sput::NvtxRange nvtx("sput_scene_create");
     if (!out) return fail(SPUT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     sput_status st = validate(desc);
@@ -590,6 +591,9 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.n_inst = (int)S->dinst.size();
     p.n_bm = (int)bm.size();
     p.n_w_total = S->n_w_smem;
+    p.n_w_all = (int)S->wtab.size();
+    p.n_rt_all = (int)S->rt.size();
+    p.n_lt_all = (int)S->lt.size();
     p.bm_lo = bt ? (float)bt->lo : 0.0f;
     p.bm_inv_h = bt ? (float)(1.0 / bt->h) : 1.0f;
     for (int a = 0; a < 3; ++a) {
@@ -643,6 +647,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
 
 sput_status sput_instances_set(sput_scene* S, const sput_instance* instances, int n)
 {
+    sput::NvtxRange nvtx("sput_instances_set");
     if (!S || !instances) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     if (n != (int)S->instances.size()) return fail(SPUT_ERR_INVALID_ARG, "number of instances must not change");
     for (int i = 0; i < n; ++i)
@@ -726,7 +731,8 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     if (threads < 32 || threads > 256 || threads % 32) return fail(SPUT_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
     int chunk = opts->ticket_chunk ? opts->ticket_chunk : S->def_chunk;
     if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
-    if (opts->flags & ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS | SPUT_RUN_LAUNCH_AT_CUTOFF))
+    if (opts->flags &
+        ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS | SPUT_RUN_LAUNCH_AT_CUTOFF | SPUT_RUN_INJECT_NONFINITE))
         return fail(SPUT_ERR_INVALID_ARG, "unknown flags");
     const int cutoff = opts->flags & SPUT_RUN_LAUNCH_AT_CUTOFF;
     const int fsm = opts->flags & (SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS);
@@ -758,6 +764,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     p.status = reinterpret_cast<unsigned int*>(scratch + 1 + kNumStats);
     p.smem_counters = (flags & SPUT_RUN_NO_SMEM_COUNTERS) ? 0 : S->smem_counters_fit;
     p.launch_at_cutoff = cutoff ? 1 : 0;
+    p.inject_nonfinite = (opts->flags & SPUT_RUN_INJECT_NONFINITE) ? 1 : 0;
 
     const TallySizes sz = tally_sizes(S);
     if (!opts->accumulate) {
@@ -837,6 +844,7 @@ extern "C" {
 sput_status sput_run(sput_scene* S, const sput_run_opts* opts, void* stream, const sput_tallies* T,
                      sput_run_stats* stats)
 {
+    sput::NvtxRange nvtx("sput_run");
     if (!S) return fail(SPUT_ERR_INVALID_ARG, "scene is NULL");
     DeviceGuard guard(S->device);
     sput_status st = ensure_scratch(S);
@@ -846,6 +854,7 @@ sput_status sput_run(sput_scene* S, const sput_run_opts* opts, void* stream, con
 
 sput_status sput_run_host(sput_scene* S, const sput_run_opts* opts, const sput_tallies* H, sput_run_stats* stats)
 {
+    sput::NvtxRange nvtx("sput_run_host");
     if (!S || !opts || !H) return fail(SPUT_ERR_INVALID_ARG, "NULL argument");
     if (H->records) return fail(SPUT_ERR_UNSUPPORTED, "records are device-only; use sput_run");
     DeviceGuard guard(S->device);
@@ -894,6 +903,7 @@ sput_status sput_run_host(sput_scene* S, const sput_run_opts* opts, const sput_t
 sput_status sput_run_noalloc(sput_scene* S, const sput_run_opts* opts, void* stream, const sput_tallies* T,
                              sput_run_stats* stats)
 {
+    sput::NvtxRange nvtx("sput_run_noalloc");
     // Same transport as sput_run, but the run scratch (ticket counter, statistics,
     // status word) is the library's static device array instead of a per-scene
     // cudaMalloc, and the statistics wait polls the stream instead of creating

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "sput.h"
 
@@ -119,6 +120,7 @@ struct Params {
     const float* lt_tab;               // joint launch-table CDFs (see DevCathode::lt_off)
     int n_prims, n_geoms, n_pairs, n_inst;
     int n_bm, n_w_total;               // n_w_total: leading w_tab entries (K, M) staged in shared memory
+    int n_w_all, n_rt_all, n_lt_all;   // entries of w_tab, rt_tab and lt_tab (bounds of the checked build)
     float bm_lo, bm_inv_h;
     float box_lo[3], box_hi[3];
     float s_gas;
@@ -150,6 +152,7 @@ struct Params {
     int smem_counters;                 // prim/timed-out counters privatised in shared memory
     int launch_at_cutoff;              // launch energy = E_max (SPUT_RUN_LAUNCH_AT_CUTOFF)
     float E_switch;                    // eV; below it after a collision the atom turns diffusive (0 = off)
+    int inject_nonfinite;              // SPUT_RUN_INJECT_NONFINITE: particle 0 of each instance starts with a NaN speed
     // scratch (library-owned device memory)
     unsigned long long* ticket_counter;
     unsigned long long* stats;         // [particles, landed, timed_out, flights, collisions, attempts]
@@ -173,6 +176,15 @@ int probe_launch(const Params& p, int what, int idx, int n, const double* x_dev,
 
 // Device copy of the scene's instance table (for the adjoint kernels).
 const DevInstance* scene_device_instances(const sput_scene* scene);
+
+// NVTX range over one entry point (scene upload, run, backward): shows the
+// library's calls on a profiler timeline; header-only, no cost without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Error text for sput_last_error from other translation units.
 void set_last_error(const char* msg);

@@ -59,6 +59,27 @@ __device__ __noinline__ uint4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint
 // RN in ]0,1]: ((x >> 8) + 1) 2^-24, exact in FP32
 __device__ __forceinline__ float rn(uint32_t x) { return (float)((x >> 8) + 1u) * 5.9604644775390625e-8f; }
 
+// ------------------------------------------------------------- checked build
+// Built with SPUT_CHECKED, every table window, cell, primitive, instance,
+// counter and record index is tested against its buffer before the access: an
+// index outside sets kStatusBadIndex in the run's status word and the access
+// is skipped (a read falls back to index 0, a write is dropped), so the run
+// ends normally and the call reports SPUT_ERR_DEVICE_CHECK.  The regular build
+// compiles every test to true.
+__device__ __forceinline__ bool idx_ok(unsigned int* status, long long i, long long n)
+{
+#ifdef SPUT_CHECKED
+    if (i >= 0 && i < n) return true;
+    if (status) atomicOr(status, kStatusBadIndex);  // the probe kernel runs without a status word
+    return false;
+#else
+    (void)status;
+    (void)i;
+    (void)n;
+    return true;
+#endif
+}
+
 // ------------------------------------------------------------- tables
 __device__ __forceinline__ float cubic_eval(const float4* tab, int n, float x)
 {
@@ -77,7 +98,9 @@ struct TableView {
     const float4* gm;  // Gauss-Mehler nodes: kGMHalf of the kGMNodes rule, then kGMHalfLo of the kGMNodesLo rule
     const DevPair* pairs;
     int n_bm;
+    int n_w;           // entries of w (bounds of the checked build)
     float bm_lo, bm_inv_h;
+    unsigned int* status;
 };
 
 __device__ __forceinline__ float bmax_eval(const TableView& T, float ln_eps)
@@ -97,6 +120,7 @@ __device__ __forceinline__ float xh_eval(const TableView& T, float ln_eps)
 __device__ __forceinline__ float wtab_eval(const TableView& T, const DevPair& pr, int off, float v)
 {
     float w = log1pf(v * pr.inv_s);
+    if (!idx_ok(T.status, (long long)off + pr.n_w - 1, T.n_w) || !idx_ok(T.status, off, T.n_w)) return 0.0f;
     return cubic_eval(T.w + off, pr.n_w, w * pr.w_inv_h);
 }
 
@@ -204,7 +228,8 @@ struct Lane {
     unsigned long long ticket;
 };
 
-__device__ __forceinline__ float racetrack_r(const DevCathode& C, const float4* rt_tab, int rt_n, float u)
+__device__ __forceinline__ float racetrack_r(const DevCathode& C, const float4* rt_tab, int rt_n, int n_rt_all,
+                                            unsigned int* status, float u)
 {
     // inverse radial CDF: cubic pieces in sqrt(u) below the median, in
     // sqrt(1-u) above it (1 - u is exact for RN = m 2^-24)
@@ -213,7 +238,9 @@ __device__ __forceinline__ float racetrack_r(const DevCathode& C, const float4* 
     const float x = sqrtf(q) * ((float)rt_n * 1.41421356237309515f);
     const int i = min((int)x, rt_n - 1);
     const float t = x - (float)i;
-    const float4 c = rt_tab[C.rt_tab + (upper ? rt_n : 0) + i];
+    int k = C.rt_tab + (upper ? rt_n : 0) + i;
+    if (!idx_ok(status, k, n_rt_all)) k = 0;
+    const float4 c = rt_tab[k];
     return fminf(fmaxf(fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x), 0.0f), C.rt_R);
 }
 
@@ -274,11 +301,12 @@ __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t ins
     const DevCathode& C = P.cath[I.cathode];
     const uint4 w0 = philox(P.key0, P.key1, pid, inst, 0u, 0u);
     const uint4 w1 = philox(P.key0, P.key1, pid, inst, 0u, 1u);
-    const float r = racetrack_r(C, rt_tab, P.rt_n, rn(w0.x));
+    const float r = racetrack_r(C, rt_tab, P.rt_n, P.n_rt_all, P.status, rn(w0.x));
     float sa, ca;
     sincospif(2.0f * rn(w0.y), &sa, &ca);
     float mu;
-    if (C.lt_off >= 0) {
+    if (C.lt_off >= 0 &&
+        idx_ok(P.status, (long long)C.lt_off + (C.lt_nmu + 1) + (long long)C.lt_nmu * (C.lt_nE + 1) - 1, P.n_lt_all)) {
         table_launch(P.lt_tab + C.lt_off, C.lt_nmu, C.lt_nE, C.lt_dE, rn(w0.w), rn(w0.z), mu, E);
     } else {
         // Thompson inverse CDF at u_E; E_max itself in a boundary run
@@ -352,8 +380,9 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
 __device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, uint32_t inst, uint32_t pid,
                                unsigned long long ticket)
 {
+    if (!idx_ok(P.status, inst, P.n_inst)) inst = 0;
     const DevInstance& I = P.inst[inst];
-    const DevGeom G = geoms[I.geometry];
+    const DevGeom G = geoms[idx_ok(P.status, I.geometry, P.n_geoms) ? I.geometry : 0];
     const DevCathode& C = P.cath[I.cathode];
     S.inst = inst;
     S.pid = pid;
@@ -362,12 +391,15 @@ __device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, u
     S.gcount = G.count;
     S.gsub = G.substrate;
     S.target = C.target;
-    S.pair = I.pair;
+    S.pair = idx_ok(P.status, I.pair, P.n_pairs) ? I.pair : 0;
     S.ng14 = I.ng14;
     S.E_per_v2 = C.E_per_v2;
     float E;
     launch_state(P, P.rt_tab, inst, pid, S.px, S.py, S.pz, S.dx, S.dy, S.dz, E);
     S.speed = C.v_per_sqrtE * sqrtf(E);
+    // failure-path test aid (SPUT_RUN_INJECT_NONFINITE): a non-finite state that the
+    // flight step retires with the non-finite status bit
+    if (P.inject_nonfinite && pid == 0u) S.speed = CUDART_NAN_F;
     S.k = 0u;
     S.ncoll = 0u;
     S.score = 0.0f;
@@ -411,7 +443,9 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     float aT = 0.0f;
     if (kScoreT) {
         // (this table stays in global memory: w_tab + G_off, read through L1)
-        out.Gv = cubic_eval(P.w_tab + pr.G_off, pr.n_w, log1pf(S.speed * pr.inv_s) * pr.w_inv_h);
+        out.Gv = idx_ok(P.status, (long long)pr.G_off + pr.n_w - 1, P.n_w_all)
+                     ? cubic_eval(P.w_tab + pr.G_off, pr.n_w, log1pf(S.speed * pr.inv_s) * pr.w_inv_h)
+                     : 0.0f;
         aT = (0.5f * out.Gv - 1.0f) * P.inv_T;
     }
 
@@ -422,6 +456,7 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     const int excl = S.k == 1u ? S.target : -1;
     for (int li = 0; li < S.gcount; ++li) {
         if (li == excl) continue;
+        if (!idx_ok(P.status, S.gbegin + li, P.n_prims)) break;
         const DevPrim& Q = prims[S.gbegin + li];
         // skip a primitive whose bounding sphere lies beyond min(ell, best t): no
         // hit on it can be the landing (margin covers FP32 rounding)
@@ -533,7 +568,8 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
             const float ua = rn(lowb);
             const float gx = o_vx - cx, gy = o_vy - cy, gz = o_vz - cz;
             const float g2 = gx * gx + gy * gy + gz * gz;
-            acc = ua * o_M <= h_of_g(T, pairs[o_pair], sqrtf(g2), g2) || a == A - 1;
+            const int op = idx_ok(T.status, o_pair, P.n_pairs) ? o_pair : 0;
+            acc = ua * o_M <= h_of_g(T, pairs[op], sqrtf(g2), g2) || a == A - 1;
         }
         const unsigned accm = __ballot_sync(kFull, acc);
         const bool is_owner = (pending >> lane) & 1u;
@@ -728,8 +764,10 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     T.gm = s_gm;
     T.pairs = s_pairs;
     T.n_bm = P.n_bm;
+    T.n_w = P.n_w_total;
     T.bm_lo = P.bm_lo;
     T.bm_inv_h = P.bm_inv_h;
+    T.status = P.status;
 
     const int lane = threadIdx.x & 31;
     const unsigned lane_lt = (1u << lane) - 1u;
@@ -817,7 +855,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                     cosang = -dn;
                 }
             }
-            if (cell >= 0) {
+            if (cell >= 0 && idx_ok(P.status, (long long)S.inst * ncell + cell, (long long)P.n_inst * ncell)) {
                 const size_t ci = (size_t)S.inst * ncell + cell;
                 if (P.counts) {
                     if (kCount64) atomicAdd(reinterpret_cast<unsigned long long*>(P.counts) + ci, 1ull);
@@ -836,10 +874,13 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                     atomicAdd(reinterpret_cast<unsigned long long*>(P.hist_A) + (size_t)S.inst * P.n_abins + b, 1ull);
                 }
             }
-            if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + hb], 1u);
+            if (!idx_ok(P.status, hb, P.max_prims)) {
+                // dropped: the checked build reports it
+            } else if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + hb], 1u);
             else if (P.prim_counts)
                 atomicAdd(reinterpret_cast<unsigned long long*>(P.prim_counts) + (size_t)S.inst * P.max_prims + hb, 1ull);
-            if (P.records) {
+            if (P.records && idx_ok(P.status, (long long)(S.ticket - P.ticket_begin),
+                                    (long long)(P.ticket_end - P.ticket_begin))) {
                 sput_record rec;
                 rec.prim = hb;
                 rec.cell = cell;
@@ -856,7 +897,8 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
             if (so.nonfinite) atomicOr(P.status, kStatusNonFinite);
             if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + P.max_prims], 1u);
             else if (P.timed_out) atomicAdd(reinterpret_cast<unsigned long long*>(P.timed_out) + S.inst, 1ull);
-            if (P.records) {
+            if (P.records && idx_ok(P.status, (long long)(S.ticket - P.ticket_begin),
+                                    (long long)(P.ticket_end - P.ticket_begin))) {
                 sput_record rec;
                 rec.prim = -1;
                 rec.cell = -1;
@@ -914,8 +956,10 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
     T.gm = s_gm;
     T.pairs = P.pairs;
     T.n_bm = P.n_bm;
+    T.n_w = P.n_w_all;
     T.bm_lo = P.bm_lo;
     T.bm_inv_h = P.bm_inv_h;
+    T.status = P.status;
     if (what == SPUT_PROBE_TRACE) {
         // state after each flight of particle x[i] of instance idx, kTraceRows rows of 10;
         // the flight step is warp-collective, so lanes past n take part without a particle

@@ -33,10 +33,11 @@ def declared_functions():
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert "sput_run" in names and "sput_scene_create" in names
-    out = subprocess.run(["nm", "-D", "--defined-only", N.LIB_PATH], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (sput_\w+)", out))
-    missing = [n for n in names if n not in exported]
-    assert not missing, missing
+    for path in (N.LIB_PATH, N.CHECKED_LIB_PATH):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+        exported = set(re.findall(r"\bT (sput_\w+)", out))
+        missing = [n for n in names if n not in exported]
+        assert not missing, (path, missing)
     for n in names:
         assert hasattr(lib, n)
     assert set(names) == set(N.SIGNATURES), set(names) ^ set(N.SIGNATURES)
