@@ -26,7 +26,12 @@ Parity status of each oracle function (pins in tests/test_oracle_*.py):
   collision kinematics     pinned: momentum/energy invariants; hard-sphere
                            uniform energy loss
   partner weighting        pinned: thermalisation to the collision-weighted
-                           Maxwellian
+                           Maxwellian (and a first-proposal-only partner
+                           fails it); the partner's relative-speed law against
+                           quadrature of sigma(g) g times the Maxwellian
+                           relative-speed density; mean attempts against the
+                           envelope's (A + B E[rho]) / K(v); the envelope
+                           bounds sigma(g) g over every reachable g
   pressure score (LR)      pinned: d/d ln p of the uncollided fraction,
                            -2 kappa E_2(kappa) (closed form); central
                            finite differences of the landing fractions with
@@ -86,19 +91,23 @@ def lib():
             L.or_scene_set_score_T.argtypes = [p, i]
             L.or_scene_set_at_cutoff.restype = None
             L.or_scene_set_at_cutoff.argtypes = [p, i]
+            L.or_scene_plant_unweighted_partner.restype = None
+            L.or_scene_plant_unweighted_partner.argtypes = [p, i]
             for name, args in {
                 "or_chi": [i, d, d], "or_x0": [i, d, d], "or_chi_hard_sphere": [d],
                 "or_bmax_direct": [i, d, d], "or_bmax_interp": [d, d],
                 "or_emax": [d, d, d, d, d], "or_racetrack_cdf": [d, d, d, d],
                 "or_racetrack_r": [d, d, d, d], "or_thompson": [d, d, d], "or_cos_mu": [p, d],
                 "or_c_energy": [], "or_s_gas": [p], "or_n_gas": [p, i], "or_inst_emax": [p, i],
-                "or_cath_ascr": [p, i], "or_sigma": [p, i, d], "or_K": [p, i, d], "or_M": [p, i, d],
+                "or_cath_ascr": [p, i], "or_sigma": [p, i, d], "or_K": [p, i, d],
                 "or_lambda": [p, i, d], "or_rel_speed_pdf": [d, d, d], "or_integrate_test": [i, d, d],
                 "or_dlnK_dlns": [p, i, d], "or_sigma_m": [p, i, d], "or_sigma_D": [p, i],
             }.items():
                 f = getattr(L, name)
                 f.restype = d
                 f.argtypes = args
+            L.or_envelope.restype = None
+            L.or_envelope.argtypes = [p, i, d, p, p]
             L.or_cath_monotone.restype = i
             L.or_cath_monotone.argtypes = [p, i]
             L.or_hit.restype = i
@@ -265,8 +274,11 @@ class OracleScene:
     def K(self, cath, v):
         return lib().or_K(self.h, cath, v)
 
-    def M(self, cath, v):
-        return lib().or_M(self.h, cath, v)
+    def envelope(self, cath, v):
+        """(A, B) of the partner-rejection envelope A + B |V|/s at atom speed v (km/s)."""
+        A, B = C.c_double(), C.c_double()
+        lib().or_envelope(self.h, cath, v, C.byref(A), C.byref(B))
+        return A.value, B.value
 
     def lam(self, inst, v):
         return lib().or_lambda(self.h, inst, v)
@@ -324,6 +336,10 @@ class OracleScene:
         mu, E = C.c_double(), C.c_double()
         lib().or_table_launch(self.h, int(cath), float(u_mu), float(u_E), C.byref(mu), C.byref(E))
         return mu.value, E.value
+
+    def plant_unweighted_partner(self, on=True):
+        """Tests only: plant a known mistake (partner drawn from the plain Maxwellian)."""
+        lib().or_scene_plant_unweighted_partner(self.h, 1 if on else 0)
 
     def set_at_cutoff(self, on):
         """Launch at E = E_max in launch() and the runs that follow (boundary runs)."""

@@ -21,8 +21,11 @@
  *     at T; n_g = p / (k_B T).
  *   - sigma(E_r) = pi b_max^2 with chi(E_r, b_max) = chi_min (CM-angle cut-off).
  *   - the gas partner is drawn from the Maxwellian weighted by sigma(g) g by
- *     rejection against M(v) = max_{0<=g<=v+6s} sigma(g) g, s = sqrt(kT/m_gas);
- *     at most A attempts, the last one is taken if none is accepted.
+ *     rejection from the Maxwellian weighted by an envelope A + B |V|/s of
+ *     sigma(g) g (s = sqrt(kT/m_gas); the line through the upper concave hull
+ *     of the largest sigma(g) g a partner of speed |V| can give, see
+ *     envelope()); at most A attempts, the last one is taken if none is
+ *     accepted.
  *   - b = b_max sqrt(RN), azimuth 2 pi RN; the azimuth is measured in the
  *     orthonormal basis of Duff et al., "Building an Orthonormal Basis,
  *     Revisited", JCGT 6(1), 2017.
@@ -434,6 +437,7 @@ typedef struct or_scene {
     int interaction, gas_motion, max_attempts;
     int want_score_T; /* compute the temperature score (or_scene_set_score_T) */
     int at_cutoff;    /* launch every atom with E = E_max (boundary run of d/dE_max) */
+    int plant_unweighted; /* tests only: a planted mistake, the partner is the plain Maxwellian */
     double E_switch;  /* eV: diffusion shortcut below it (0 = off) */
     int64_t max_collisions;
     double hs_diameter;
@@ -529,17 +533,55 @@ static double lambda_m(const or_scene* S, const cath_t* c, const inst_t* I, doub
 
 static double h_of_g(const or_scene* S, const cath_t* c, double g) { return sigma_of_g(S, c, g) * g; }
 
-/* rejection bound M(v) = max_{0 <= g <= v + 6 s} sigma(g) g */
-static double M_of_v(const or_scene* S, const cath_t* c, double v)
+/* Envelope of the gas-partner rejection (reading of the paper's gas motion).
+ * A partner of speed rho s (rho = |V|/s) meets the atom at a relative speed g
+ * in [|v - s rho|, v + s rho], so h(g) = sigma(g) g <= H(rho), the largest h
+ * over [max(0, v - s rho), v + s rho], which does not decrease with rho.  The
+ * envelope is the line A + B rho above H on [0, ENV_RHO_MAX] with the least
+ * value at rho = ENV_M = E[rho] under the Maxwellian (the mean of the chi
+ * distribution with 3 degrees of freedom, 2 sqrt(2/pi)): the line through the
+ * edge of H's upper concave hull that spans ENV_M, with H taken at ENV_N + 1
+ * equally spaced rho and the line raised by the relative margin ENV_MARGIN.
+ * The expected number of attempts per partner is (A + B ENV_M) / K(v). */
+#define ENV_N 512
+#define ENV_RHO_MAX 8.0
+#define ENV_MARGIN 1e-4
+static const double ENV_M = 1.5957691216057308;
+
+static void envelope(const or_scene* S, const cath_t* c, double v, double* A, double* B)
 {
-    double G = v + 6.0 * S->s_gas;
-    if (c->h_monotone) return h_of_g(S, c, G);
-    double m = h_of_g(S, c, G);
-    for (int i = 1; i < 4000; ++i) {
-        double hv = h_of_g(S, c, G * i / 4000.0);
-        if (hv > m) m = hv;
+    const double s = S->s_gas;
+    double rho[ENV_N + 1], H[ENV_N + 1];
+    double hm = h_of_g(S, c, v);
+    for (int k = 0; k <= ENV_N; ++k) {
+        rho[k] = ENV_RHO_MAX * k / ENV_N;
+        double hi = h_of_g(S, c, v + s * rho[k]);
+        if (hi > hm) hm = hi;
+        double glo = v - s * rho[k];
+        if (glo > 0.0) {
+            double lo = h_of_g(S, c, glo);
+            if (lo > hm) hm = lo;
+        }
+        H[k] = hm;
     }
-    return m;
+    /* upper concave hull of (rho_k, H_k), rho increasing (monotone chain) */
+    int hull[ENV_N + 1], nh = 0;
+    for (int k = 0; k <= ENV_N; ++k) {
+        while (nh >= 2) {
+            int i = hull[nh - 2], j = hull[nh - 1];
+            double cross = (rho[j] - rho[i]) * (H[k] - H[i]) - (H[j] - H[i]) * (rho[k] - rho[i]);
+            if (cross >= 0.0) --nh; /* j on or below the chord i -> k */
+            else break;
+        }
+        hull[nh++] = k;
+    }
+    int e = 0;
+    while (e + 2 < nh && rho[hull[e + 1]] <= ENV_M) ++e;
+    int i = hull[e], j = hull[e + 1];
+    double b = (H[j] - H[i]) / (rho[j] - rho[i]);
+    double a = H[i] - b * rho[i];
+    *A = a * (1.0 + ENV_MARGIN);
+    *B = b * (1.0 + ENV_MARGIN);
 }
 
 /* ---------------------------------------------- diffusion shortcut (opt-in) */
@@ -774,10 +816,19 @@ static void collide_with(const or_scene* S, const cath_t* c, const double v[3], 
     if (chi_out) *chi_out = chi;
 }
 
-/* gas partner: Maxwellian weighted by sigma(g) g, by rejection.  Attempt a
- * draws Philox block 1 + a of the flight's event: the upper 24 bits of its four
- * words give the Box-Muller pairs (three components used), and the low bytes of
- * words 0, 1, 2, joined into one more 24-bit number, the acceptance uniform. */
+/* Gas partner: the Maxwellian f(V) weighted by h(g) = sigma(g) g, g = |v - V|,
+ * by rejection from the proposal f(V) (A + B rho) of the envelope above: the
+ * Maxwellian with weight A and, with weight B ENV_M, its rho-weighted form, whose
+ * speed has the chi distribution with 4 degrees of freedom; accepted with
+ * probability h(g) / (A + B rho).  Attempt a draws Philox block 1 + a of the
+ * flight's event.  The upper 24 bits of its four words give two Box-Muller pairs,
+ * z = (z1, z2, z3, z4) standard normal.  The low bytes of words 0, 1, 2, joined
+ * into one 24-bit number, give u: u (A + B ENV_M) <= B ENV_M selects the rho-
+ * weighted branch, and u, rescaled to (0, 1] inside the selected branch, is the
+ * acceptance uniform.  Maxwellian branch: V = s (z1, z2, z3).  Weighted branch:
+ * V = s |z| (z1, z2, z3) / |(z1, z2, z3)| (the direction of (z1, z2, z3) is
+ * uniform and independent of |z|).  At most A attempts; the last is kept if none
+ * is accepted. */
 static int sample_partner(const or_scene* S, const cath_t* c, const stream_t* st, uint32_t event, const double v[3],
                           double V[3])
 {
@@ -785,22 +836,42 @@ static int sample_partner(const or_scene* S, const cath_t* c, const stream_t* st
         V[0] = V[1] = V[2] = 0.0;
         return 0;
     }
+    if (S->plant_unweighted) {
+        /* planted mistake for the tests that must detect it: no sigma(g) g weighting */
+        uint32_t w[4];
+        draw(st, event, 1u, w);
+        double R0 = sqrt(-2.0 * log(rn(w[0]))), R1 = sqrt(-2.0 * log(rn(w[2])));
+        V[0] = S->s_gas * R0 * cos(2.0 * M_PI * rn(w[1]));
+        V[1] = S->s_gas * R0 * sin(2.0 * M_PI * rn(w[1]));
+        V[2] = S->s_gas * R1 * cos(2.0 * M_PI * rn(w[3]));
+        return 1;
+    }
     double speed = sqrt(dot3(v, v));
-    double Mv = M_of_v(S, c, speed);
+    double Aenv, Benv;
+    envelope(S, c, speed, &Aenv, &Benv);
+    const double Bm = Benv * ENV_M, tot = Aenv + Bm;
     double s = S->s_gas;
     int A = S->max_attempts;
     uint32_t w[4];
     for (int a = 0; a < A; ++a) {
         draw(st, event, 1u + (uint32_t)a, w);
         double R0 = sqrt(-2.0 * log(rn(w[0]))), R1 = sqrt(-2.0 * log(rn(w[2])));
-        V[0] = s * R0 * cos(2.0 * M_PI * rn(w[1]));
-        V[1] = s * R0 * sin(2.0 * M_PI * rn(w[1]));
-        V[2] = s * R1 * cos(2.0 * M_PI * rn(w[3]));
+        double z1 = R0 * cos(2.0 * M_PI * rn(w[1])), z2 = R0 * sin(2.0 * M_PI * rn(w[1]));
+        double z3 = R1 * cos(2.0 * M_PI * rn(w[3])), z4 = R1 * sin(2.0 * M_PI * rn(w[3]));
         uint32_t low = ((w[0] & 0xffu) << 24) | ((w[1] & 0xffu) << 16) | ((w[2] & 0xffu) << 8);
-        double ua = rn(low);
+        double ut = rn(low) * tot;
+        double r3 = sqrt(z1 * z1 + z2 * z2 + z3 * z3);
+        int weighted = ut <= Bm;
+        double rho = weighted ? sqrt(r3 * r3 + z4 * z4) : r3;
+        double scale = weighted ? (r3 > 0.0 ? rho / r3 : 0.0) : 1.0;
+        V[0] = s * scale * z1;
+        V[1] = s * scale * z2;
+        V[2] = s * scale * z3;
         double gv[3] = {v[0] - V[0], v[1] - V[1], v[2] - V[2]};
-        double g = sqrt(dot3(gv, gv));
-        if (ua * Mv <= h_of_g(S, c, g)) return a + 1;
+        double hg = h_of_g(S, c, sqrt(dot3(gv, gv)));
+        double env = Aenv + Benv * rho;
+        /* weighted: u' = ut / Bm; Maxwellian: u' = (ut - Bm) / Aenv; accept if u' env <= h */
+        if (weighted ? ut * env <= Bm * hg : (ut - Bm) * env <= Aenv * hg) return a + 1;
     }
     return A;
 }
@@ -1207,6 +1278,7 @@ int or_version(void) { return OR_VERSION; }
 void or_scene_set_score_T(or_scene* S, int on) { S->want_score_T = on; }
 /* launch every atom at the Thompson cut-off E_max from now on (boundary runs) */
 void or_scene_set_at_cutoff(or_scene* S, int on) { S->at_cutoff = on; }
+void or_scene_plant_unweighted_partner(or_scene* S, int on) { S->plant_unweighted = on; }
 double or_dlnK_dlns(const or_scene* S, int cath, double v) { return dlnK_dlns(S, &S->cath[cath], v); }
 double or_sigma_m(const or_scene* S, int cath, double g) { return sigma_m_of_g(S, &S->cath[cath], g); }
 double or_sigma_D(const or_scene* S, int cath) { return sigma_D_of(S, &S->cath[cath]); }
@@ -1218,7 +1290,7 @@ double or_cath_ascr(const or_scene* S, int c) { return S->cath[c].a_scr; }
 int or_cath_monotone(const or_scene* S, int c) { return S->cath[c].h_monotone; }
 double or_sigma(const or_scene* S, int c, double g) { return sigma_of_g(S, &S->cath[c], g); }
 double or_K(const or_scene* S, int c, double v) { return K_of_v(S, &S->cath[c], v); }
-double or_M(const or_scene* S, int c, double v) { return M_of_v(S, &S->cath[c], v); }
+void or_envelope(const or_scene* S, int c, double v, double* A, double* B) { envelope(S, &S->cath[c], v, A, B); }
 double or_lambda(const or_scene* S, int inst, double v)
 {
     return lambda_m(S, &S->cath[S->inst[inst].cathode], &S->inst[inst], v);

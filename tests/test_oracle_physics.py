@@ -158,16 +158,68 @@ def test_K_stationary_limit(oracle_mod):
         assert abs(o.lam(0, v) * n_mm3 * o.sigma(0, v) * 1e-14 - 1.0) < 1e-12
 
 
-def test_majorant_bounds_h(oracle_mod):
-    """The rejection bound M(v) >= sigma(g) g for every g <= v + 6 s."""
+ENV_M = 2.0 * math.sqrt(2.0 / math.pi)   # mean speed / s of the Maxwellian (chi, 3 degrees of freedom)
+
+
+def test_envelope_bounds_h(oracle_mod):
+    """The rejection envelope A + B rho >= sigma(g) g for every relative speed g that a
+    partner of speed rho s can give (g^2 = v^2 + s^2 rho^2 - 2 v s rho cos), rho <= 8,
+    and it is nearly tight at rho = E[rho] (the upper hull of a concave bound)."""
     sc = workloads.scene_quaternary(n_per_cathode=1)
     o = oracle_mod.OracleScene(sc)
     s = o.s_gas()
     for c in range(4):
-        for v in [0.0, 0.2, 1.0, 4.0, 15.0]:
-            M = o.M(c, v)
-            for g in np.linspace(1e-6, v + 6 * s, 40):
-                assert o.sigma(c, g) * g <= M * (1 + 1e-12)
+        for v in [1e-3, 0.2, 0.5, 1.0, 4.0, 15.0]:
+            A, B = o.envelope(c, v)
+            assert A >= 0 and B >= 0
+            for rho in np.linspace(0.0, 8.0, 65):
+                for cs in np.linspace(-1.0, 1.0, 21):
+                    g = math.sqrt(max(v * v + s * s * rho * rho - 2 * v * s * rho * cs, 1e-18))
+                    assert o.sigma(c, g) * g <= (A + B * rho) * (1 + 1e-12), (c, v, rho, cs)
+            gm = np.linspace(max(0.0, v - s * ENV_M), v + s * ENV_M, 400)[1:]
+            Hm = max(o.sigma(c, g) * g for g in gm)
+            assert A + B * ENV_M <= 1.01 * Hm, (c, v, A + B * ENV_M, Hm)
+
+
+@pytest.mark.parametrize("v", [0.3, 1.2, 6.0])
+def test_partner_law_and_mean_attempts(oracle_mod, v):
+    """Partners drawn for an atom of speed v (km/s): the relative speed g = |v - V|
+    follows sigma(g) g times the Maxwellian relative-speed density (KS test against
+    the quadrature CDF), the mean partner velocity along v matches the 2-D quadrature
+    of the weighted Maxwellian, and the mean number of attempts is (A + B E[rho]) / K(v)."""
+    sc = workloads.scene_single_ni(n=1)
+    o = oracle_mod.OracleScene(sc)
+    s = o.s_gas()
+    n = 12000
+    vv = np.array([0.0, 0.0, v])
+    Vs, att = [], []
+    for pid in range(n):
+        V, a = o.partner(0, pid, 5, vv)
+        Vs.append(V)
+        att.append(a)
+    Vs, att = np.array(Vs), np.array(att, float)
+    g = np.linalg.norm(vv - Vs, axis=1)
+    h = lambda x: o.sigma(0, x) * x
+    grid = np.linspace(1e-9, v + 9 * s, 3001)
+    pdf = np.array([h(x) * oracle_mod.rel_speed_pdf(x, v, s) for x in grid])
+    cdf = integrate.cumulative_trapezoid(pdf, grid, initial=0)
+    K = cdf[-1]
+    assert abs(K / o.K(0, v) - 1) < 1e-3
+    p_ks = stats.kstest(g, lambda x: np.interp(x, grid, cdf / K)).pvalue
+    assert p_ks > 1e-3, p_ks
+    # mean of V along v: int f(V) h(|v - V|) V_par dV / K, V = s rho (sin, 0, cos)
+    f = lambda r, c: (r * r * math.exp(-0.5 * r * r) / math.sqrt(2 * math.pi) * 2 / 2)
+    num = integrate.dblquad(lambda c, r: f(r, c) * h(math.sqrt(max(v * v + s * s * r * r - 2 * v * s * r * c, 1e-18)))
+                            * s * r * c, 0, 9, -1, 1, epsabs=1e-10, epsrel=1e-8)[0]
+    den = integrate.dblquad(lambda c, r: f(r, c) * h(math.sqrt(max(v * v + s * s * r * r - 2 * v * s * r * c, 1e-18))),
+                            0, 9, -1, 1, epsabs=1e-10, epsrel=1e-8)[0]
+    want_par = num / den
+    got = Vs[:, 2]
+    assert abs(got.mean() - want_par) < 4 * got.std() / math.sqrt(n), (got.mean(), want_par)
+    A, B = o.envelope(0, v)
+    want_att = (A + B * ENV_M) / o.K(0, v)
+    assert 1.0 <= want_att < 2.0
+    assert abs(att.mean() - want_att) < 4 * att.std() / math.sqrt(n) + 1e-3, (att.mean(), want_att)
 
 
 # ------------------------------------------------------------ kinematics
@@ -206,9 +258,11 @@ def test_hard_sphere_uniform_energy_loss(oracle_mod):
         assert abs(vo @ vo / E0 - want) < 1e-12
 
 
-def _thermal_check(oracle_mod, physics, n_particles, n_coll, burn, stride, pmin):
+def _thermal_check(oracle_mod, physics, n_particles, n_coll, burn, stride, pmin, plant=False):
     sc = workloads.scene_single_ni(n=1, physics=physics)
     o = oracle_mod.OracleScene(sc)
+    if plant:
+        o.plant_unweighted_partner()
     m1, mg = 58.6934, 39.948
     kT = 8.617333262e-5 * 300.0
     ce = oracle_mod.c_energy()
@@ -240,3 +294,11 @@ def test_thermalisation_hard_sphere(oracle_mod):
 def test_thermalisation_moliere(oracle_mod):
     p = _thermal_check(oracle_mod, {}, 48, 600, 200, 40, 1e-3)
     assert p > 1e-3
+
+
+@pytest.mark.slow
+def test_thermalisation_detects_an_unweighted_partner(oracle_mod):
+    """Planted mistake: the partner drawn from the plain Maxwellian, without the
+    sigma(g) g weighting; the thermalisation test must reject it."""
+    p = _thermal_check(oracle_mod, {"interaction": "hard_sphere"}, 60, 400, 100, 10, 1e-3, plant=True)
+    assert p < 1e-3, p
