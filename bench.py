@@ -485,7 +485,7 @@ def plain_per_instance(torch, tr, sc, seed, stream, flush, collisions, batched=N
 def run_extras(args, torch, pkg, api, workloads, dev, peaks):
     out = {}
     for name, fn in (("single_ni", sub_single_ni), ("sweep", sub_sweep), ("large", sub_large),
-                     ("adjoint_vs_fd", sub_adjoint_vs_fd)):
+                     ("adjoint_vs_fd", sub_adjoint_vs_fd), ("inverse_solve", sub_inverse_solve)):
         if args.workload == name:
             continue
         t0 = time.perf_counter()
@@ -523,13 +523,29 @@ def sub_single_ni(args, torch, pkg, api, workloads, dev, peaks):
     api.sput_graph_destroy(g)
     tr.close()
     coll = sum(s["collisions"] for s in stats)
+    # the same workload repeated 100 times inside one launch (1e7 particle ids, one
+    # instance): the GPU is filled instead of waiting on the slowest atom of 1e5
+    big = workloads.scene_single_ni(n=100 * 100_000)
+    trb = pkg.Transport(big, device=dev.index)
+    trb.run(seed=98, ticket_end=1_000_000)
+    e0.record(stream)
+    stb = trb.run(seed=97, stream=stream.cuda_stream).as_dict()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_big = e0.elapsed_time(e1)
+    trb.close()
     roof = roofline_entry(stats, [s["kernel_ms"] for s in stats], mean_prims(sc), peaks)
+    roof_big = roofline_entry([stb], [stb["kernel_ms"]], mean_prims(big), peaks)
     return {"workload": WORKLOADS["single_ni"], "value": coll / (ms / 1e3), "unit": UNIT,
             "landed_per_s": sum(s["landed"] for s in stats) / (ms / 1e3),
             "launches": R, "ms_per_launch_graph": ms / R, "kernel_ms_single_launch": one_ms,
             "graph_replay_matches_sput_run": graph_ok, "roofline": roof,
             "note": "R seeds of the 1e5-atom workload replayed from one CUDA graph (seed updated per replay), "
-                    "inputs resident; kernel_ms_single_launch is one launch's own event time"}
+                    "inputs resident; kernel_ms_single_launch is one launch's own event time: a launch of 1e5 "
+                    "atoms is bound by the latency of its longest trajectories",
+            "repeated_in_one_launch": {"particles": big.total_particles, "value": stb["collisions"] / (ms_big / 1e3),
+                                       "unit": UNIT, "landed_per_s": stb["landed"] / (ms_big / 1e3), "ms": ms_big,
+                                       "roofline": roof_big}}
 
 
 def sub_sweep(args, torch, pkg, api, workloads, dev, peaks):
@@ -646,6 +662,49 @@ def sub_adjoint_vs_fd(args, torch, pkg, api, workloads, dev, peaks):
             "std": {"adjoint": dict(zip(names, np.sqrt(var_lr).tolist())),
                     "finite_differences": dict(zip(names, np.sqrt(var_fd).tolist()))},
             "cost_ratio_fd_over_adjoint_at_equal_se": dict(zip(names, ratio.tolist()))}
+
+
+def sub_inverse_solve(args, torch, pkg, api, workloads, dev, peaks):
+    """The adjoint workload at its size: 50 Adam steps of the inverse solve for (p, P_1..P_4)
+    on the quaternary scene at 1e7 atoms per cathode per step, 342-point map, Table S1 rate
+    and voltage lines, to a target transported from random true values (Table 1 ranges)
+    with its own seed; each step is a forward run with the score, the composition map, a
+    boundary run at the cut-off and the backward kernels."""
+    import numpy as np
+
+    from paper_2411_14413_gb300.adjoint import MapSetup, inverse_solve
+    from workloads import ELEMENTS
+    from workloads.measurement import POWER_RANGE, calibration_points, measurement_patches, voltage_points
+
+    quat = ("Ni", "Pd", "Pt", "Ru")
+    rng = np.random.default_rng(20241122)
+    true_p = float(math.exp(rng.uniform(math.log(0.3), math.log(1.0))))
+    true_pw = np.array([rng.uniform(*POWER_RANGE[s]) for s in quat])
+    cal, volt = [], []
+    for s in quat:
+        (p1, r1), (p2, r2) = calibration_points(s)
+        cal.append([p1, r1, p2, r2, ELEMENTS[s].density, ELEMENTS[s].mass])
+        (q1, v1), (q2, v2) = voltage_points(s)
+        volt.append([q1, v1, q2, v2])
+    patch, _pts, ref = measurement_patches()
+    sc = workloads.scene_quaternary(n_per_cathode=10_000_000)
+    ms = MapSetup(sc, patch, ref, np.array(cal), device=dev.index, voltage=np.array(volt))
+    target = ms.forward(true_p, true_pw, seed=987654).clone()
+    start = np.array([0.5 * (POWER_RANGE[s][0] + POWER_RANGE[s][1]) for s in quat])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    hist = inverse_solve(ms, target, math.log(0.5), start, steps=50, lr=0.1, seed=1)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    ms.close()
+    frac = lambda x: np.asarray(x) / np.sum(x)
+    last = hist[-1]
+    return {"setup": "quaternary, 1e7 atoms per cathode per step, 342 points, rate + voltage lines, 50 Adam steps",
+            "s_per_step": dt / 50,
+            "true": {"p": true_p, "power": true_pw.tolist()}, "fit": {"p": last["p"], "power": last["power"]},
+            "p_rel_error": last["p"] / true_p - 1.0,
+            "power_fraction_max_error": float(np.abs(frac(last["power"]) - frac(true_pw)).max()),
+            "loss": {"first": hist[0]["loss"], "last": last["loss"]}}
 
 
 def main():

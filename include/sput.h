@@ -23,8 +23,11 @@
  *   lambda_m(v) = v / (n_g <sigma(g) g>) averaged over a Maxwellian gas at T,
  *   n_g = p / (k_B T); sigma = pi b_max^2 with the CM deflection at b_max equal
  *   to chi_min; the gas partner is drawn from the Maxwellian weighted by
- *   sigma(g) g (rejection against M(v) = max over g <= v + 6 sqrt(kT/m_gas) of
- *   sigma(g) g, at most max_attempts attempts, the last attempt is kept);
+ *   sigma(g) g, by rejection from the Maxwellian weighted by a line
+ *   A(v) + B(v) |V|/s (s = sqrt(kT/m_gas)) that bounds sigma(g) g over every
+ *   relative speed a partner of speed |V| can give: the edge of the upper
+ *   concave hull of that bound spanning the Maxwellian's mean |V|/s (at most
+ *   max_attempts attempts, the last attempt is kept);
  *   impact parameter b = b_max sqrt(RN); azimuth 2 pi RN in the orthonormal
  *   basis of Duff et al. (JCGT 2017); Firsov screening length
  *   a = 0.8853 a_0 (Z1^1/2 + Z2^1/2)^(-2/3).
@@ -34,10 +37,10 @@
  * Event 0 is the launch (block 0: racetrack radius, racetrack azimuth, energy,
  * polar cosine; block 1 word 0: emission azimuth).  Event k >= 1 is flight k
  * (block 0: flight length, impact parameter, scattering azimuth; block 1+a,
- * a < max_attempts: partner attempt a, the three Maxwellian components by
- * Box-Muller from its four words, and its acceptance uniform from the low
- * bytes of words 0, 1, 2 joined as x = (w0 & 255) << 24 | (w1 & 255) << 16 |
- * (w2 & 255) << 8).  A 32-bit word x maps to RN = ((x >> 8) + 1) * 2^-24,
+ * a < max_attempts: partner attempt a, two Box-Muller pairs from its four
+ * words, and one more uniform from the low bytes of words 0, 1, 2 joined as
+ * x = (w0 & 255) << 24 | (w1 & 255) << 16 | (w2 & 255) << 8, which selects the
+ * proposal's branch and, rescaled within it, is the acceptance uniform).  A 32-bit word x maps to RN = ((x >> 8) + 1) * 2^-24,
  * which uses only its upper 24 bits.
  * Every particle therefore has its own stream: integer tallies are bit-exact
  * and independent of launch configuration, order and chunking.
@@ -483,10 +486,15 @@ void sput_scene_destroy(sput_scene* scene);
 /* Diagnostics: evaluate one step of the device code path on given inputs
  * (device functions identical to those of the transport kernel), for parity
  * tests.  `x` and `y` are HOST arrays; layouts per `what`:
- *   SPUT_PROBE_CHI      x[2n] = (eps, beta) reduced units, pair p -> y[n] = chi (rad)
+ *   SPUT_PROBE_CHI      x[2n] = (eps, beta) reduced units, pair p -> y[n] = chi (rad) by the direct
+ *                       Gauss-Mehler integration (the device's path outside the deflection table)
+ *   SPUT_PROBE_CHI_U    x[2n] = (eps, u)          -> y[n] = chi (rad) as a collision computes it from
+ *                       the impact-parameter uniform u (b = b_max(eps) sqrt(u)): the deflection
+ *                       table inside its range, the direct integration outside
  *   SPUT_PROBE_BMAX     x[n]  = eps                        -> y[n] = b_max / a
  *   SPUT_PROBE_K        x[n]  = speed (km/s), pair p       -> y[n] = <sigma g> (A^2 km/s)
- *   SPUT_PROBE_M        x[n]  = speed (km/s), pair p       -> y[n] = M(v) (A^2 km/s)
+ *   SPUT_PROBE_M        x[n]  = speed (km/s), pair p       -> y[2n] = (A, B): the partner-rejection
+ *                       envelope A + B |V|/s (A^2 km/s) at atom speed v
  *   SPUT_PROBE_LAUNCH   x[n]  = particle id, instance p    -> y[7n] = (x,y,z, dx,dy,dz, E)
  *   SPUT_PROBE_TRACE    x[n]  = particle id, instance p    -> y[640n]: 64 rows of
  *       (x,y,z, dx,dy,dz, speed, status, a, t): row 0 the launch (status -1), row r the
@@ -501,10 +509,21 @@ typedef enum sput_probe_kind {
     SPUT_PROBE_K = 2,
     SPUT_PROBE_M = 3,
     SPUT_PROBE_LAUNCH = 4,
-    SPUT_PROBE_TRACE = 5
+    SPUT_PROBE_TRACE = 5,
+    SPUT_PROBE_CHI_U = 6
 } sput_probe_kind;
 
 sput_status sput_probe(sput_scene* scene, int what, int p, int n, const double* x, double* y);
+
+/* Host evaluation, in FP64, of the deflection table the device uses for the Moliere
+ * potential (the paper's screened Coulomb interaction, Sec. "The SIMTRA model"), built
+ * once per chi_min: q = ln tan(chi/2) over x = ln eps and y = ln(b/b_max) = (ln u)/2 as
+ * bicubic cells through FP64 node values of the classical deflection integral
+ * (x in [-26, -4] step 1/4; y in [-6, -1] step 1/32 and [-1, 0] step 1/128).  For each
+ * i < n: chi[i] (rad) at reduced energy eps[i] > 0 and impact-parameter uniform
+ * 0 < u[i] <= 1; outside the table the FP64 deflection at b = b_max sqrt(u).  HOST arrays;
+ * no device is touched.  Errors: INVALID_ARG. */
+sput_status sput_deflection_table_eval(double chi_min, int n, const double* eps, const double* u, double* chi);
 
 #ifdef __cplusplus
 }

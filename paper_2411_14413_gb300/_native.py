@@ -91,7 +91,7 @@ PRIM_KIND = {"box": 0, "rect": 1, "disc": 2, "cylinder": 3}
 INTERACTION = {"moliere": 0, "hard_sphere": 1}
 GAS_MOTION = {"thermal": 0, "stationary": 1}
 COUNT_TYPE = {"int32": 0, "int64": 1}
-PROBE = {"chi": 0, "bmax": 1, "K": 2, "M": 3, "launch": 4, "trace": 5}
+PROBE = {"chi": 0, "bmax": 1, "K": 2, "M": 3, "launch": 4, "trace": 5, "chi_u": 6}
 TRACE_ROWS = 64
 
 D3 = C.c_double * 3
@@ -230,6 +230,7 @@ SIGNATURES = {
     "sput_composition_backward": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P,
                                             _P]),
     "sput_probe": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "sput_deflection_table_eval": (C.c_int, [C.c_double, C.c_int, _P, _P, _P]),
     "sput_microbench": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.c_size_t, C.c_int, _P,
                                   C.POINTER(sput_microbench_result)]),
 }

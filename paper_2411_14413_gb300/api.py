@@ -148,8 +148,8 @@ def sput_scene_destroy(handle):
 
 def sput_probe(handle, what, idx, x):
     x = np.ascontiguousarray(x, dtype=np.float64)
-    n = len(x) // 2 if what == "chi" else len(x)
-    width = {"launch": 7, "trace": N.TRACE_ROWS * 10}.get(what, 1)
+    n = len(x) // 2 if what in ("chi", "chi_u") else len(x)
+    width = {"launch": 7, "trace": N.TRACE_ROWS * 10, "M": 2}.get(what, 1)
     y = np.zeros(n * width, dtype=np.float64)
     rc = _lib().sput_probe(handle, N.PROBE[what], int(idx), int(n), x.ctypes.data_as(C.c_void_p),
                            y.ctypes.data_as(C.c_void_p))

@@ -100,7 +100,6 @@ struct sput_scene {
     std::vector<std::vector<double>> lt_weights;  // copies of the cathodes' joint launch tables
     std::vector<float> lt;                        // their CDFs (DevCathode::lt_off)
     std::vector<PairPhys> pair_phys;
-    std::vector<int> pair_monotone;
     std::vector<double> pair_E_top;
     const BmaxTable* bt = nullptr;
     double s_gas = 0.0;
@@ -109,7 +108,7 @@ struct sput_scene {
     // device memory
     unsigned char* d_blob = nullptr;
     size_t off_prims = 0, off_geoms = 0, off_cath = 0, off_pairs = 0, off_inst = 0, off_prefix = 0, off_bm = 0,
-           off_xh = 0, off_w = 0, off_rt = 0, off_lt = 0, blob_bytes = 0;
+           off_xh = 0, off_w = 0, off_rt = 0, off_lt = 0, off_chi = 0, blob_bytes = 0;
     // run scratch (allocated on the first run): ticket counter, stats, status word
     unsigned long long* d_scratch = nullptr;
     unsigned long long* h_scratch = nullptr;  // pinned
@@ -399,15 +398,14 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         top = std::max(top, std::max(2.0 * Em, 200.0));
     }
     S->dpairs.resize(S->pair_phys.size());
-    S->pair_monotone.resize(S->pair_phys.size());
     const double h_w = 0.02;
     std::vector<std::vector<float4>> g_tabs(S->pair_phys.size());
     for (size_t p = 0; p < S->pair_phys.size(); ++p) {
         const PairPhys& pp = S->pair_phys[p];
         double v_top = std::sqrt(2.0 * S->pair_E_top[p] / (pp.m1 * kEnergyUnit)) + 12.0 * S->s_gas;
-        std::vector<float4> K, M, Gt;
+        std::vector<float4> K, EA, EB, Gt;
         int n_w = 0;
-        build_w_tables(pp, S->bt, S->s_gas, thermal, v_top, h_w, K, M, Gt, n_w);
+        build_w_tables(pp, S->bt, S->s_gas, thermal, v_top, h_w, K, EA, EB, Gt, n_w);
         DevPair& D = S->dpairs[p];
         D.kappa = (float)pp.kappa;
         D.ln_kappa = (float)std::log(pp.kappa);
@@ -417,17 +415,18 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         D.hard_sphere = hard ? 1 : 0;
         D.K_off = (int)S->wtab.size();
         S->wtab.insert(S->wtab.end(), K.begin(), K.end());
-        D.M_off = (int)S->wtab.size();
-        S->wtab.insert(S->wtab.end(), M.begin(), M.end());
+        D.A_off = (int)S->wtab.size();
+        S->wtab.insert(S->wtab.end(), EA.begin(), EA.end());
+        D.B_off = (int)S->wtab.size();
+        S->wtab.insert(S->wtab.end(), EB.begin(), EB.end());
         g_tabs[p] = std::move(Gt);
         D.sigma_D = S->physics.thermal_switch_eV > 0.0 ? (float)sigma_D64(pp, S->bt, S->chamber.gas_T) : 0.0f;
-        D.pad_d[0] = D.pad_d[1] = D.pad_d[2] = 0.0f;
+        D.pad_d[0] = D.pad_d[1] = 0.0f;
         D.n_w = n_w;
         D.w_inv_h = (float)(1.0 / h_w);
         D.inv_s = (float)(1.0 / S->s_gas);
-        S->pair_monotone[p] = h_monotone(pp, S->bt, v_top + 20.0 * S->s_gas);
     }
-    // the d ln K/d ln s tables follow every K and M table: only K and M are staged in
+    // the d ln K/d ln s tables follow every K, A and B table: only K, A and B are staged in
     // shared memory; the temperature-score instance reads these from global memory
     S->n_w_smem = (int)S->wtab.size();
     for (size_t p = 0; p < S->pair_phys.size(); ++p) {
@@ -542,6 +541,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->off_w = place(sizeof(float4) * S->wtab.size());
     S->off_rt = place(sizeof(float4) * S->rt.size());
     S->off_lt = place(sizeof(float) * S->lt.size());
+    const ChiTable* ct = hard ? nullptr : &chi_table(S->physics.chi_min);
+    S->off_chi = place(ct ? sizeof(float4) * ct->cells.size() : 0);
     S->blob_bytes = o;
     cudaError_t e = cudaMalloc(&S->d_blob, S->blob_bytes);
     if (e != cudaSuccess) {
@@ -563,6 +564,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     put(S->off_w, S->wtab.data(), sizeof(float4) * S->wtab.size());
     put(S->off_rt, S->rt.data(), sizeof(float4) * S->rt.size());
     put(S->off_lt, S->lt.data(), sizeof(float) * S->lt.size());
+    if (ct) put(S->off_chi, ct->cells.data(), sizeof(float4) * ct->cells.size());
     e = cudaMemcpy(S->d_blob, h.data(), S->blob_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_scratch, 64);
     if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
@@ -585,6 +587,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.w_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_w);
     p.rt_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_rt);
     p.lt_tab = reinterpret_cast<const float*>(S->d_blob + S->off_lt);
+    p.chi_tab = ct ? reinterpret_cast<const float4*>(S->d_blob + S->off_chi) : nullptr;
     p.n_prims = (int)S->dprims.size();
     p.n_geoms = (int)S->dgeoms.size();
     p.n_pairs = (int)S->dpairs.size();
@@ -1152,20 +1155,42 @@ void sput_scene_destroy(sput_scene* S)
     delete S;
 }
 
+sput_status sput_deflection_table_eval(double chi_min, int n, const double* eps, const double* u, double* chi)
+{
+    if (!eps || !u || !chi || n < 0) return fail(SPUT_ERR_INVALID_ARG, "NULL argument or negative n");
+    if (!(chi_min > 0.0 && chi_min < 0.5 * kPi)) return fail(SPUT_ERR_INVALID_ARG, "chi_min must be in (0, pi/2)");
+    const ChiTable& ct = chi_table(chi_min);
+    const BmaxTable& bt = bmax_table(chi_min);
+    for (int i = 0; i < n; ++i) {
+        if (!(eps[i] > 0.0) || !(u[i] > 0.0 && u[i] <= 1.0)) return fail(SPUT_ERR_INVALID_ARG, "need eps > 0, 0 < u <= 1");
+        double q;
+        if (ct.eval(std::log(eps[i]), 0.5 * std::log(u[i]), q)) {
+            chi[i] = 2.0 * std::atan(std::exp(q));
+        } else {
+            // outside the table the device integrates; here the FP64 deflection
+            chi[i] = chi_moliere64(eps[i], bt.eval(std::log(eps[i])) * std::sqrt(u[i]));
+        }
+    }
+    return SPUT_OK;
+}
+
 sput_status sput_probe(sput_scene* S, int what, int idx, int n, const double* x, double* y)
 {
     if (!S || !x || !y || n < 0) return fail(SPUT_ERR_INVALID_ARG, "NULL argument or negative n");
-    if (what < SPUT_PROBE_CHI || what > SPUT_PROBE_TRACE) return fail(SPUT_ERR_INVALID_ARG, "unknown probe");
+    if (what < SPUT_PROBE_CHI || what > SPUT_PROBE_CHI_U) return fail(SPUT_ERR_INVALID_ARG, "unknown probe");
     if ((what == SPUT_PROBE_K || what == SPUT_PROBE_M) && (idx < 0 || idx >= (int)S->dpairs.size()))
         return fail(SPUT_ERR_INVALID_ARG, "pair index out of range");
     if ((what == SPUT_PROBE_LAUNCH || what == SPUT_PROBE_TRACE) && (idx < 0 || idx >= (int)S->dinst.size()))
         return fail(SPUT_ERR_INVALID_ARG, "instance index out of range");
-    if ((what == SPUT_PROBE_CHI || what == SPUT_PROBE_BMAX) && !S->bt)
+    if ((what == SPUT_PROBE_CHI || what == SPUT_PROBE_BMAX || what == SPUT_PROBE_CHI_U) && !S->bt)
         return fail(SPUT_ERR_UNSUPPORTED, "no Moliere tables in a hard-sphere scene");
     if (n == 0) return SPUT_OK;
     DeviceGuard guard(S->device);
-    const size_t nx = (size_t)n * (what == SPUT_PROBE_CHI ? 2 : 1);
-    const size_t ny = (size_t)n * (what == SPUT_PROBE_LAUNCH ? 7 : (what == SPUT_PROBE_TRACE ? kTraceRows * 10 : 1));
+    const size_t nx = (size_t)n * (what == SPUT_PROBE_CHI || what == SPUT_PROBE_CHI_U ? 2 : 1);
+    const size_t ny = (size_t)n * (what == SPUT_PROBE_LAUNCH   ? 7
+                                   : what == SPUT_PROBE_TRACE  ? kTraceRows * 10
+                                   : what == SPUT_PROBE_M      ? 2
+                                                               : 1);
     double *dx = nullptr, *dy = nullptr;
     CUDA_TRY(cudaMalloc(&dx, nx * sizeof(double)));
     cudaError_t e = cudaMalloc(&dy, ny * sizeof(double));

@@ -25,12 +25,30 @@ constexpr float kGMLoLnEps = -7.0f;
 // < 2e-8 relative within 5 steps over the whole eps, b range; one spare).
 constexpr int kApsisIters = 6;
 
+// Deflection table of the Moliere potential, q = ln tan(chi/2) over
+// x = ln eps and y = ln(b / b_max(eps)) (b_max: chi(eps, b_max) = chi_min), bicubic
+// cells: x in [kChiX0, kChiX0 + kChiNx kChiHx] in steps of kChiHx; y in [kChiY0, kChiY1]
+// in steps of kChiHyC, then in [kChiY1, 0] in steps of kChiHyF, where screening
+// makes chi fall from tenths of a radian to chi_min over a few hundredths of y at
+// small eps.  Outside (rare) the device integrates the deflection directly.  The
+// steps are powers of two, so node positions and cell indices are exact in FP32.
+constexpr float kChiX0 = -26.0f, kChiHx = 0.25f;
+constexpr int kChiNx = 88;
+constexpr float kChiY0 = -6.0f, kChiY1 = -1.0f, kChiHyC = 0.03125f, kChiHyF = 0.0078125f;
+constexpr int kChiNyC = 160, kChiNyF = 128, kChiNy = kChiNyC + kChiNyF;
+constexpr int kChiCells = kChiNx * kChiNy;
+
 // Moliere screening: Phi(x) = sum c_i exp(-d_i x) (Moliere 1947).
 constexpr float kMolC0 = 0.35f, kMolC1 = 0.55f, kMolC2 = 0.10f;
 constexpr float kMolD0 = 0.3f, kMolD1 = 1.2f, kMolD2 = 6.0f;
 
-// Rejection bound window: M(v) = max over g <= v + kMajorantSigmas * s of sigma(g) g.
-constexpr double kMajorantSigmas = 6.0;
+// Envelope of the gas-partner rejection (see envelope64 in sput_tables.h): H sampled at
+// kEnvN + 1 points of rho = |V|/s in [0, kEnvRhoMax], the line raised by kEnvMargin;
+// kEnvM = 2 sqrt(2/pi), the mean of |V|/s under the Maxwellian.
+constexpr int kEnvN = 512;
+constexpr double kEnvRhoMax = 8.0;
+constexpr double kEnvMargin = 1e-4;
+constexpr double kEnvM = 1.5957691216057308;
 
 // Device status bits (sput_run_stats.device_status).
 enum : uint32_t {
@@ -84,13 +102,14 @@ struct alignas(16) DevPair {
     float m1M;          // m1 / (m1 + m2)
     float m2M;          // m2 / (m1 + m2)
     int hard_sphere;
-    int K_off, M_off;   // float4 offsets of the <sigma g>(w) and M(w) tables
+    int K_off;          // float4 offset of the <sigma g>(w) table
+    int A_off, B_off;   // float4 offsets of the rejection-envelope coefficient tables A(w), B(w)
     int n_w;            // intervals of the w tables
     float w_inv_h;      // 1 / Delta w
     float inv_s;        // 1 / s_gas, w = ln(1 + v / s_gas)
     int G_off;          // float4 offset of the d ln K / d ln s table (zero for a gas at rest)
     float sigma_D;      // diffusion cross section (A^2) of the thermalised-atom shortcut: 1/lambda_D = n sigma_D
-    float pad_d[3];
+    float pad_d[2];
 };
 
 struct alignas(16) DevInstance {
@@ -118,6 +137,7 @@ struct Params {
     const float4* w_tab;               // all pairs' K and M pieces, then their d ln K/d ln s pieces
     const float4* rt_tab;              // racetrack inverse-CDF pieces (2 rt_n per cathode)
     const float* lt_tab;               // joint launch-table CDFs (see DevCathode::lt_off)
+    const float4* chi_tab;             // deflection table: kChiCells cells of 4 float4 (null: hard spheres)
     int n_prims, n_geoms, n_pairs, n_inst;
     int n_bm, n_w_total;               // n_w_total: leading w_tab entries (K, M) staged in shared memory
     int n_w_all, n_rt_all, n_lt_all;   // entries of w_tab, rt_tab and lt_tab (bounds of the checked build)

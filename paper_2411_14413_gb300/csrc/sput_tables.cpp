@@ -225,6 +225,159 @@ const BmaxTable& bmax_table(double chi_min)
     return *T;
 }
 
+namespace {
+
+// Slopes of the C2 cubic spline through (t_i, f_i), i < n (n >= 4), with the end
+// slopes of the cubic through the four end nodes; t strictly increasing.
+void spline_slopes(const double* t, const double* f, int n, double* s)
+{
+    auto end_slope = [](const double* tt, const double* ff, int at) {
+        // derivative at tt[at] of the Lagrange cubic through the four points
+        double d = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            double num = 0.0, den = 1.0;
+            for (int m = 0; m < 4; ++m)
+                if (m != k) den *= tt[k] - tt[m];
+            for (int m = 0; m < 4; ++m) {
+                if (m == k) continue;
+                double prod = 1.0;
+                for (int r = 0; r < 4; ++r)
+                    if (r != k && r != m) prod *= tt[at] - tt[r];
+                num += prod;
+            }
+            d += ff[k] * num / den;
+        }
+        return d;
+    };
+    s[0] = end_slope(t, f, 0);
+    s[n - 1] = end_slope(t + n - 4, f + n - 4, 3);
+    // h_i s_{i-1} + 2 (h_{i-1} + h_i) s_i + h_{i-1} s_{i+1} = 3 (h_i d_{i-1} + h_{i-1} d_i)
+    std::vector<double> a(n), b(n), c(n), r(n);
+    for (int i = 1; i < n - 1; ++i) {
+        const double h0 = t[i] - t[i - 1], h1 = t[i + 1] - t[i];
+        const double d0 = (f[i] - f[i - 1]) / h0, d1 = (f[i + 1] - f[i]) / h1;
+        a[i] = h1;
+        b[i] = 2.0 * (h0 + h1);
+        c[i] = h0;
+        r[i] = 3.0 * (h1 * d0 + h0 * d1);
+    }
+    r[1] -= a[1] * s[0];
+    r[n - 2] -= c[n - 2] * s[n - 1];
+    for (int i = 2; i < n - 1; ++i) {  // Thomas elimination
+        const double w = a[i] / b[i - 1];
+        b[i] -= w * c[i - 1];
+        r[i] -= w * r[i - 1];
+    }
+    s[n - 2] = r[n - 2] / b[n - 2];
+    for (int i = n - 3; i >= 1; --i) s[i] = (r[i] - c[i] * s[i + 1]) / b[i];
+}
+
+}  // namespace
+
+bool ChiTable::eval(double ln_eps, double ln_s, double& q) const
+{
+    const double fx = (ln_eps - kChiX0) / kChiHx;
+    if (!(fx >= 0.0 && fx < kChiNx) || !(ln_s >= kChiY0) || ln_s > 0.0) return false;
+    const int i = std::min((int)fx, kChiNx - 1);
+    const double tx = fx - i;
+    int j;
+    double ty;
+    if (ln_s < kChiY1) {
+        const double fy = (ln_s - kChiY0) / kChiHyC;
+        j = std::min((int)fy, kChiNyC - 1);
+        ty = fy - j;
+    } else {
+        const double fy = (ln_s - kChiY1) / kChiHyF;
+        j = std::min((int)fy, kChiNyF - 1);
+        ty = fy - j;
+        j += kChiNyC;
+    }
+    const double* a = &a64[16 * ((size_t)i * kChiNy + j)];
+    double p = 0.0;
+    for (int k = 3; k >= 0; --k) {
+        const double ck = a[4 * k] + ty * (a[4 * k + 1] + ty * (a[4 * k + 2] + ty * a[4 * k + 3]));
+        p = p * tx + ck;
+    }
+    q = p;
+    return true;
+}
+
+const ChiTable& chi_table(double chi_min)
+{
+    static std::mutex mu;
+    static std::map<double, ChiTable*> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(chi_min);
+    if (it != cache.end()) return *it->second;
+    // nodes of the table's cells plus kExt more on every side: the splines' end
+    // slopes then fall outside the stored cells (y > 0 is b > b_max, chi < chi_min)
+    constexpr int kExt = 4;
+    const int NX = kChiNx + 1 + 2 * kExt, NY = kChiNy + 1 + 2 * kExt;
+    std::vector<double> X(NX), Y(NY);
+    for (int i = 0; i < NX; ++i) X[i] = kChiX0 + (double)kChiHx * (i - kExt);
+    for (int j = 0; j < NY; ++j) {
+        const int k = j - kExt;  // node index of the table's own grid
+        Y[j] = k <= kChiNyC ? kChiY0 + (double)kChiHyC * k : kChiY1 + (double)kChiHyF * (k - kChiNyC);
+    }
+    const int j_zero = kExt + kChiNy;  // the node y = 0, b = b_max
+    // node values q = ln tan(chi/2) at b = b_max(eps) e^y, rows of x in parallel
+    std::vector<double> Q((size_t)NX * NY), Qx(Q.size()), Qy(Q.size()), Qxy(Q.size());
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            for (int i = (int)t; i < NX; i += (int)nt) {
+                const double eps = std::exp(X[i]);
+                const double bm = bmax64(eps, chi_min);
+                for (int j = 0; j < NY; ++j) {
+                    const double chi = j == j_zero ? chi_min : chi_moliere64(eps, bm * std::exp(Y[j]));
+                    Q[(size_t)i * NY + j] = std::log(std::tan(0.5 * chi));
+                }
+            }
+        });
+    for (auto& x : th) x.join();
+    std::vector<double> col(NX), sl(std::max(NX, NY));
+    for (int i = 0; i < NX; ++i) spline_slopes(Y.data(), &Q[(size_t)i * NY], NY, &Qy[(size_t)i * NY]);
+    for (int j = 0; j < NY; ++j) {
+        for (int i = 0; i < NX; ++i) col[i] = Q[(size_t)i * NY + j];
+        spline_slopes(X.data(), col.data(), NX, sl.data());
+        for (int i = 0; i < NX; ++i) Qx[(size_t)i * NY + j] = sl[i];
+        for (int i = 0; i < NX; ++i) col[i] = Qy[(size_t)i * NY + j];
+        spline_slopes(X.data(), col.data(), NX, sl.data());
+        for (int i = 0; i < NX; ++i) Qxy[(size_t)i * NY + j] = sl[i];
+    }
+    // cubic Hermite basis in power form: value and slope at t = 0, value and slope at t = 1
+    static const double H[4][4] = {{1, 0, -3, 2}, {0, 1, -2, 1}, {0, 0, 3, -2}, {0, 0, -1, 1}};
+    ChiTable* T = new ChiTable();
+    T->chi_min = chi_min;
+    T->a64.assign((size_t)kChiCells * 16, 0.0);
+    T->cells.resize((size_t)kChiCells * 4);
+    for (int i = 0; i < kChiNx; ++i)
+        for (int j = 0; j < kChiNy; ++j) {
+            const int ni = i + kExt, nj = j + kExt;
+            const double dx = X[ni + 1] - X[ni], dy = Y[nj + 1] - Y[nj];
+            double* a = &T->a64[16 * ((size_t)i * kChiNy + j)];
+            for (int ci = 0; ci < 2; ++ci)
+                for (int cj = 0; cj < 2; ++cj) {
+                    const size_t n = (size_t)(ni + ci) * NY + (nj + cj);
+                    // (value, y slope; x slope, cross slope) scaled to the cell's unit square
+                    const double v[2][2] = {{Q[n], Qy[n] * dy}, {Qx[n] * dx, Qxy[n] * dx * dy}};
+                    for (int dxo = 0; dxo < 2; ++dxo)
+                        for (int dyo = 0; dyo < 2; ++dyo) {
+                            const double* hx = H[2 * ci + dxo];
+                            const double* hy = H[2 * cj + dyo];
+                            for (int k = 0; k < 4; ++k)
+                                for (int l = 0; l < 4; ++l) a[4 * k + l] += v[dxo][dyo] * hx[k] * hy[l];
+                        }
+                }
+            for (int k = 0; k < 4; ++k)
+                T->cells[4 * ((size_t)i * kChiNy + j) + k] =
+                    make_float4((float)a[4 * k], (float)a[4 * k + 1], (float)a[4 * k + 2], (float)a[4 * k + 3]);
+        }
+    cache[chi_min] = T;
+    return *T;
+}
+
 PairPhys make_pair(double Z1, double m1, double Z2, double m2, int hard_sphere, double hs_d, double chi_min)
 {
     PairPhys p;
@@ -279,36 +432,46 @@ double K64(const PairPhys& pp, const BmaxTable* bt, double s, int thermal, doubl
     return sum;
 }
 
-int h_monotone(const PairPhys& pp, const BmaxTable* bt, double g_top)
+void envelope64(const PairPhys& pp, const BmaxTable* bt, double s, double v, double& A, double& B)
 {
-    double prev = 0.0;
-    for (int j = 1; j <= 4000; ++j) {
-        double g = g_top * j / 4000.0, hv = sigma64(pp, bt, g) * g;
-        if (hv < prev) return 0;
-        prev = hv;
+    // H(rho): the largest h = sigma(g) g over [max(0, v - s rho), v + s rho], sampled at
+    // kEnvN + 1 equally spaced rho in [0, kEnvRhoMax]
+    double rho[kEnvN + 1], H[kEnvN + 1];
+    double hm = sigma64(pp, bt, v) * v;
+    for (int k = 0; k <= kEnvN; ++k) {
+        rho[k] = kEnvRhoMax * k / kEnvN;
+        const double gh = v + s * rho[k];
+        hm = std::max(hm, sigma64(pp, bt, gh) * gh);
+        const double gl = v - s * rho[k];
+        if (gl > 0.0) hm = std::max(hm, sigma64(pp, bt, gl) * gl);
+        H[k] = hm;
     }
-    return 1;
-}
-
-double M64(const PairPhys& pp, const BmaxTable* bt, double s, double v, int monotone)
-{
-    double G = v + kMajorantSigmas * s;
-    double m = sigma64(pp, bt, G) * G;
-    if (monotone) return m;
-    for (int j = 1; j < 4000; ++j) {
-        double g = G * j / 4000.0;
-        m = std::max(m, sigma64(pp, bt, g) * g);
+    // the edge of the upper concave hull of (rho, H) that spans kEnvM
+    int hull[kEnvN + 1], nh = 0;
+    for (int k = 0; k <= kEnvN; ++k) {
+        while (nh >= 2) {
+            const int i = hull[nh - 2], j = hull[nh - 1];
+            const double cross = (rho[j] - rho[i]) * (H[k] - H[i]) - (H[j] - H[i]) * (rho[k] - rho[i]);
+            if (cross >= 0.0) --nh;
+            else break;
+        }
+        hull[nh++] = k;
     }
-    return m;
+    int e = 0;
+    while (e + 2 < nh && rho[hull[e + 1]] <= kEnvM) ++e;
+    const int i = hull[e], j = hull[e + 1];
+    const double b = (H[j] - H[i]) / (rho[j] - rho[i]);
+    A = (H[i] - b * rho[i]) * (1.0 + kEnvMargin);
+    B = b * (1.0 + kEnvMargin);
 }
 
 void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s, int thermal, double v_top, double h_w,
-                    std::vector<float4>& K, std::vector<float4>& M, std::vector<float4>& G, int& n_w)
+                    std::vector<float4>& K, std::vector<float4>& EA, std::vector<float4>& EB, std::vector<float4>& G,
+                    int& n_w)
 {
     double w_top = std::log1p(v_top / s);
     n_w = std::max(4, (int)std::ceil(w_top / h_w));
-    int mono = h_monotone(pp, bt, v_top + 20.0 * s);
-    std::vector<double> kv(3 * n_w + 1), mv(3 * n_w + 1), gv(3 * n_w + 1);
+    std::vector<double> kv(3 * n_w + 1), av(3 * n_w + 1), bv(3 * n_w + 1), gv(3 * n_w + 1);
     unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     std::vector<std::thread> th;
     for (unsigned t = 0; t < nt; ++t)
@@ -318,7 +481,8 @@ void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s, int therm
                 // stationary gas: tabulate sigma(v) = K(v)/v, so that the inverse mean free
                 // path n sigma(v) stays finite when the speed decays towards zero
                 kv[j] = thermal ? K64(pp, bt, s, 1, v) : sigma64(pp, bt, v);
-                mv[j] = thermal ? M64(pp, bt, s, v, mono) : 0.0;
+                av[j] = bv[j] = 0.0;
+                if (thermal) envelope64(pp, bt, s, v, av[j], bv[j]);
                 // d ln K / d ln s at fixed v by a central difference in s (gas at rest: 0)
                 const double hs = 1e-4;
                 gv[j] = thermal ? (K64(pp, bt, s * (1.0 + hs), 1, v) - K64(pp, bt, s * (1.0 - hs), 1, v)) /
@@ -328,11 +492,13 @@ void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s, int therm
         });
     for (auto& x : th) x.join();
     K.resize(n_w);
-    M.resize(n_w);
+    EA.resize(n_w);
+    EB.resize(n_w);
     G.resize(n_w);
     for (int i = 0; i < n_w; ++i) {
         K[i] = cubic_from_thirds(kv[3 * i], kv[3 * i + 1], kv[3 * i + 2], kv[3 * i + 3]);
-        M[i] = cubic_from_thirds(mv[3 * i], mv[3 * i + 1], mv[3 * i + 2], mv[3 * i + 3]);
+        EA[i] = cubic_from_thirds(av[3 * i], av[3 * i + 1], av[3 * i + 2], av[3 * i + 3]);
+        EB[i] = cubic_from_thirds(bv[3 * i], bv[3 * i + 1], bv[3 * i + 2], bv[3 * i + 3]);
         G[i] = cubic_from_thirds(gv[3 * i], gv[3 * i + 1], gv[3 * i + 2], gv[3 * i + 3]);
     }
 }

@@ -36,6 +36,22 @@ struct BmaxTable {
 // Cached per chi_min (thread-safe).
 const BmaxTable& bmax_table(double chi_min);
 
+// Deflection table (layout constants kChi* in sput_internal.h): node values
+// q = ln tan(chi/2) from the FP64 deflection at b = b_max(eps) e^y; slopes in x,
+// y and the cross slope from C2 cubic splines through the nodes (end slopes from
+// the cubic through the four end nodes); each cell the bicubic Hermite patch of
+// its four corners, stored as p(tx, ty) = sum_k tx^k sum_l a[k][l] ty^l,
+// tx, ty in [0, 1], row k of the cell in float4 k.
+struct ChiTable {
+    double chi_min = 0.0;
+    std::vector<float4> cells;       // 4 per cell, cell (i, j) at 4 (i kChiNy + j)
+    std::vector<double> a64;         // the same coefficients in FP64, 16 per cell
+    // FP64 evaluation of the same cells; returns false outside the table
+    bool eval(double ln_eps, double ln_s, double& q) const;
+};
+
+const ChiTable& chi_table(double chi_min);
+
 // Reduced-unit Moliere scattering: closest approach and CM deflection (FP64).
 double head_on_apsis64(double eps);
 double apsis64(double eps, double beta);
@@ -56,11 +72,19 @@ PairPhys make_pair(double Z1, double m1, double Z2, double m2, int hard_sphere, 
 // sigma(g) in Angstrom^2 (g in km/s)
 double sigma64(const PairPhys& pp, const BmaxTable* bt, double g);
 
+// Envelope of the gas-partner rejection at atom speed v: the line A + B rho (rho = |V|/s)
+// above H(rho), the largest sigma(g) g over [max(0, v - s rho), v + s rho], on
+// [0, kEnvRhoMax], with the least value at rho = kEnvM (the Maxwellian's mean |V|/s):
+// the edge of H's upper concave hull that spans kEnvM, from H at kEnvN + 1 equally
+// spaced rho, raised by the relative margin kEnvMargin.
+void envelope64(const PairPhys& pp, const BmaxTable* bt, double s_gas, double v, double& A, double& B);
+
 // Tables in w = ln(1 + v/s) with pieces of width h_w up to w(v_top):
-// K(v) = <sigma(g) g> over the Maxwellian gas (gas at rest: sigma(v) = K(v)/v) and the
-// rejection bound M(v) = max_{g <= v + 6 s} sigma(g) g.
+// K(v) = <sigma(g) g> over the Maxwellian gas (gas at rest: sigma(v) = K(v)/v), the
+// envelope coefficients A(v), B(v) and G(v) = d ln K / d ln s.
 void build_w_tables(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v_top,
-                    double h_w, std::vector<float4>& K, std::vector<float4>& M, std::vector<float4>& G, int& n_w);
+                    double h_w, std::vector<float4>& K, std::vector<float4>& EA, std::vector<float4>& EB,
+                    std::vector<float4>& G, int& n_w);
 
 // Momentum-transfer cross section sigma_m(g) = 2 pi int_0^inf (1 - cos chi) b db (Angstrom^2)
 // and the diffusion cross section sigma_D (Angstrom^2) of the shortcut for thermalised atoms:
@@ -71,8 +95,7 @@ double sigma_D64(const PairPhys& pp, const BmaxTable* bt, double T);
 
 // FP64 host values used by tests through the probe entry point.
 double K64(const PairPhys& pp, const BmaxTable* bt, double s_gas, int gas_thermal, double v);
-double M64(const PairPhys& pp, const BmaxTable* bt, double s_gas, double v, int monotone);
-int h_monotone(const PairPhys& pp, const BmaxTable* bt, double g_top);
+
 
 // Racetrack inverse CDF: n cubic pieces in sqrt(u), then n in sqrt(1-u), over [0, sqrt(1/2)].
 void racetrack_table(double r0, double sigma, double R, int n, float4* out);

@@ -116,12 +116,16 @@ __device__ __forceinline__ float xh_eval(const TableView& T, float ln_eps)
     return fmaf(t, T.xh[i + 1] - T.xh[i], T.xh[i]);
 }
 
-// K(v) or M(v) of a pair: cubic pieces in w = ln(1 + v/s)
-__device__ __forceinline__ float wtab_eval(const TableView& T, const DevPair& pr, int off, float v)
+// K(v), A(v) or B(v) of a pair: cubic pieces in w = ln(1 + v/s), at a given w
+__device__ __forceinline__ float wtab_at(const TableView& T, const DevPair& pr, int off, float w)
 {
-    float w = log1pf(v * pr.inv_s);
     if (!idx_ok(T.status, (long long)off + pr.n_w - 1, T.n_w) || !idx_ok(T.status, off, T.n_w)) return 0.0f;
     return cubic_eval(T.w + off, pr.n_w, w * pr.w_inv_h);
+}
+
+__device__ __forceinline__ float wtab_eval(const TableView& T, const DevPair& pr, int off, float v)
+{
+    return wtab_at(T, pr, off, log1pf(v * pr.inv_s));
 }
 
 // sigma(g) g in A^2 km/s
@@ -205,6 +209,49 @@ __device__ float chi_over_pi_moliere(float eps, float ln_eps, float beta, float 
         s += __fdividef(D, S * (S + bt));
     }
     return s * (lo ? 2.0f / (float)kGMNodesLo : 2.0f / (float)kGMNodes);
+}
+
+// Deflection from the table: q = ln tan(chi/2) at x = ln eps, y = ln(b/b_max) (y <= 0),
+// bicubic in the cell; false outside the table (the caller integrates instead).
+__device__ __forceinline__ bool chi_table_q(const float4* tab, unsigned int* status, float x, float y, float& q)
+{
+    const float fx = (x - kChiX0) * (1.0f / kChiHx);
+    if (!(fx >= 0.0f && fx < (float)kChiNx && y >= kChiY0)) return false;
+    const int i = min((int)fx, kChiNx - 1);
+    const float tx = fx - (float)i;
+    int j;
+    float ty;
+    if (y < kChiY1) {
+        const float fy = (y - kChiY0) * (1.0f / kChiHyC);
+        j = min((int)fy, kChiNyC - 1);
+        ty = fy - (float)j;
+    } else {
+        const float fy = (y - kChiY1) * (1.0f / kChiHyF);
+        j = min((int)fy, kChiNyF - 1);
+        ty = fminf(fy - (float)j, 1.0f);
+        j += kChiNyC;
+    }
+    const int cell = i * kChiNy + j;
+    if (!idx_ok(status, cell, kChiCells)) return false;
+    const float4* c = tab + 4 * cell;
+    const float4 r0 = __ldg(c), r1 = __ldg(c + 1), r2 = __ldg(c + 2), r3 = __ldg(c + 3);
+    const float c0 = fmaf(ty, fmaf(ty, fmaf(ty, r0.w, r0.z), r0.y), r0.x);
+    const float c1 = fmaf(ty, fmaf(ty, fmaf(ty, r1.w, r1.z), r1.y), r1.x);
+    const float c2 = fmaf(ty, fmaf(ty, fmaf(ty, r2.w, r2.z), r2.y), r2.x);
+    const float c3 = fmaf(ty, fmaf(ty, fmaf(ty, r3.w, r3.z), r3.y), r3.x);
+    q = fmaf(tx, fmaf(tx, fmaf(tx, c3, c2), c1), c0);
+    return true;
+}
+
+// cos and sin of the deflection from q = ln tan(chi/2): with T = e^q,
+// cos chi = (1 - T^2)/(1 + T^2), sin chi = 2T/(1 + T^2)
+__device__ __forceinline__ void chi_cos_sin(float q, float& cc, float& sc)
+{
+    const float Tq = expf(fminf(q, 40.0f));
+    const float T2 = Tq * Tq;
+    const float inv = 1.0f / (1.0f + T2);
+    cc = (1.0f - T2) * inv;
+    sc = 2.0f * Tq * inv;
 }
 
 // orthonormal pair perpendicular to unit n (Duff et al., JCGT 6(1), 2017)
@@ -503,17 +550,25 @@ __device__ __forceinline__ int nth_set_bit(unsigned mask, int n)
 }
 
 // Gas partners of every lane with `need`, drawn by the whole warp: the
-// Maxwellian weighted by sigma(g) g by rejection against M(v).  Attempt a of a
-// particle uses its own Philox block 1 + a: the upper 24 bits of the four words
-// give the three Box-Muller components, the low bytes of words 0-2 the
-// acceptance uniform; the first accepted attempt is kept (attempt A-1 if none
-// is).  Each round spreads the pending particles' next attempts over all 32
-// lanes (consecutive attempts per particle, the first 32 mod np particles one
-// more), so the result is the sequential rejection loop's result while every
-// lane stays busy.  Must be called by all 32 lanes together.
+// Maxwellian f(V) weighted by h(g) = sigma(g) g, by rejection from the
+// proposal f(V) (EA + EB rho), rho = |V|/s, where EA + EB rho bounds h over the
+// relative speeds a partner of speed rho s can give (the pair's envelope tables
+// at the atom's speed).  The proposal is the Maxwellian with weight EA and, with
+// weight EB E[rho], its rho-weighted form, whose speed follows the chi law with
+// 4 degrees of freedom.  Attempt a of a particle uses its own Philox block 1 + a:
+// the upper 24 bits of the four words give two Box-Muller pairs z1..z4, the low
+// bytes of words 0-2 one more uniform u that selects the branch
+// (u (EA + EB E[rho]) <= EB E[rho]: rho-weighted) and, rescaled within the
+// branch, is the acceptance uniform.  Maxwellian branch: V = s (z1, z2, z3);
+// rho-weighted branch: V = s |z| (z1, z2, z3)/|(z1, z2, z3)|.  The first
+// accepted attempt is kept (attempt A-1 if none is).  Each round spreads the
+// pending particles' next attempts over all 32 lanes (consecutive attempts per
+// particle, the first 32 mod np particles one more), so the result is the
+// sequential rejection loop's result while every lane stays busy.  Must be
+// called by all 32 lanes together.
 __device__ void partner_sample_warp(bool need, const Params& P, const TableView& T, const DevPair* pairs,
                                     uint32_t pid, uint32_t inst, uint32_t k, int pair, float vx, float vy, float vz,
-                                    float M, float& Vx, float& Vy, float& Vz, int& attempts)
+                                    float EA, float EB, float& Vx, float& Vy, float& Vz, int& attempts)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -548,7 +603,8 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         const float o_vx = __shfl_sync(kFull, vx, owner);
         const float o_vy = __shfl_sync(kFull, vy, owner);
         const float o_vz = __shfl_sync(kFull, vz, owner);
-        const float o_M = __shfl_sync(kFull, M, owner);
+        const float o_A = __shfl_sync(kFull, EA, owner);
+        const float o_B = __shfl_sync(kFull, EB, owner);
         const int o_next = __shfl_sync(kFull, next_a, owner);
         const int a = o_next + j;
         bool acc = false;
@@ -557,19 +613,29 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
             const uint4 wn = philox(P.key0, P.key1, o_pid, o_inst, o_k, 1u + (uint32_t)a);
             const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
             const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
-            float s1, c1;
+            float s1, c1, s3, c3;
             sincospif(2.0f * rn(wn.y), &s1, &c1);
-            const float c3 = cospif(2.0f * rn(wn.w));
-            cx = P.s_gas * R0 * c1;
-            cy = P.s_gas * R0 * s1;
-            cz = P.s_gas * R1 * c3;
+            sincospif(2.0f * rn(wn.w), &s3, &c3);
+            const float z1 = R0 * c1, z2 = R0 * s1, z3 = R1 * c3, z4 = R1 * s3;
             // low bytes of words 0, 1, 2 as one more 24-bit uniform
             const uint32_t lowb = ((wn.x & 0xffu) << 24) | ((wn.y & 0xffu) << 16) | ((wn.z & 0xffu) << 8);
-            const float ua = rn(lowb);
+            const float Bm = o_B * (float)kEnvM;
+            const float ut = rn(lowb) * (o_A + Bm);
+            const bool weighted = ut <= Bm;
+            const float r32 = z1 * z1 + z2 * z2 + z3 * z3;
+            const float r3 = sqrtf(r32);
+            const float rho = weighted ? sqrtf(r32 + z4 * z4) : r3;
+            const float sc = P.s_gas * (weighted ? (r3 > 0.0f ? rho / r3 : 0.0f) : 1.0f);
+            cx = sc * z1;
+            cy = sc * z2;
+            cz = sc * z3;
             const float gx = o_vx - cx, gy = o_vy - cy, gz = o_vz - cz;
             const float g2 = gx * gx + gy * gy + gz * gz;
             const int op = idx_ok(T.status, o_pair, P.n_pairs) ? o_pair : 0;
-            acc = ua * o_M <= h_of_g(T, pairs[op], sqrtf(g2), g2) || a == A - 1;
+            const float hg = h_of_g(T, pairs[op], sqrtf(g2), g2);
+            const float env = fmaf(o_B, rho, o_A);
+            // the branch's own uniform, rescaled to (0, 1], times the envelope against h
+            acc = (weighted ? ut * env <= Bm * hg : (ut - Bm) * env <= o_A * hg) || a == A - 1;
         }
         const unsigned accm = __ballot_sync(kFull, acc);
         const bool is_owner = (pending >> lane) & 1u;
@@ -612,17 +678,21 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
         const float g = sqrtf(g2);
         const float ig = 1.0f / g;
         const float hx = gx * ig, hy = gy * ig, hz = gz * ig;
-        float chi_pi;  // deflection / pi
+        float sc, cc, sp, cp;
+        const float ub = rn(w.y);  // impact parameter b = b_max sqrt(ub)
+        float q;
         if (pr.hard_sphere) {
-            chi_pi = acosf(sqrtf(rn(w.y))) * (2.0f / 3.14159265358979f);
+            sincospif(acosf(sqrtf(ub)) * (2.0f / 3.14159265358979f), &sc, &cc);
         } else {
             const float eps = pr.kappa * g2;
             const float le = logf(eps);
-            const float beta = bmax_eval(T, le) * sqrtf(rn(w.y));
-            chi_pi = chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm);
+            if (chi_table_q(P.chi_tab, P.status, le, 0.5f * logf(ub), q)) {
+                chi_cos_sin(q, cc, sc);
+            } else {
+                const float beta = bmax_eval(T, le) * sqrtf(ub);
+                sincospif(chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm), &sc, &cc);
+            }
         }
-        float sc, cc, sp, cp;
-        sincospif(chi_pi, &sc, &cc);
         sincospif(2.0f * rn(w.z), &sp, &cp);
         float3 b1, b2;
         onb(hx, hy, hz, b1, b2);
@@ -662,8 +732,13 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
     const float vx = S.speed * S.dx, vy = S.speed * S.dy, vz = S.speed * S.dz;
     float Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
     if (P.gas_thermal) {
-        const float M = coll ? wtab_eval(T, pr, pr.M_off, S.speed) : 0.0f;
-        partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, M, Vx, Vy, Vz,
+        float EA = 0.0f, EB = 0.0f;
+        if (coll) {
+            const float w = log1pf(S.speed * pr.inv_s);
+            EA = wtab_at(T, pr, pr.A_off, w);
+            EB = wtab_at(T, pr, pr.B_off, w);
+        }
+        partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, EA, EB, Vx, Vy, Vz,
                             out.attempts);
         // partner density f_T(V) sigma(g) g / K(v): d ln/dT = (|V|^2/(2 s^2) - 3/2 - G/2)/T
         if (kScoreT && coll)
@@ -1005,14 +1080,31 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         const float eps = (float)x[2 * i], beta = (float)x[2 * i + 1];
         const float le = logf(eps);
         y[i] = 3.141592653589793 * (double)chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm);
+    } else if (what == SPUT_PROBE_CHI_U) {
+        // the collision's path: table inside its range, direct integration outside
+        const float eps = (float)x[2 * i], ub = (float)x[2 * i + 1];
+        const float le = logf(eps);
+        float q;
+        if (chi_table_q(P.chi_tab, P.status, le, 0.5f * logf(ub), q)) {
+            y[i] = 2.0 * atan(exp((double)q));
+        } else {
+            const float beta = bmax_eval(T, le) * sqrtf(ub);
+            y[i] = 3.141592653589793 * (double)chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm);
+        }
     } else if (what == SPUT_PROBE_BMAX) {
         y[i] = bmax_eval(T, logf((float)x[i]));
-    } else if (what == SPUT_PROBE_K || what == SPUT_PROBE_M) {
+    } else if (what == SPUT_PROBE_K) {
         const DevPair pr = P.pairs[idx];
         const float v = (float)x[i];
-        float val = wtab_eval(T, pr, what == SPUT_PROBE_K ? pr.K_off : pr.M_off, v);
-        if (what == SPUT_PROBE_K && !P.gas_thermal) val *= v;  // the table holds sigma(v) = K/v
+        float val = wtab_eval(T, pr, pr.K_off, v);
+        if (!P.gas_thermal) val *= v;  // the table holds sigma(v) = K/v
         y[i] = val;
+    } else if (what == SPUT_PROBE_M) {
+        // rejection envelope (A, B) of the pair at speed v
+        const DevPair pr = P.pairs[idx];
+        const float w = log1pf((float)x[i] * pr.inv_s);
+        y[2 * i] = wtab_at(T, pr, pr.A_off, w);
+        y[2 * i + 1] = wtab_at(T, pr, pr.B_off, w);
     } else if (what == SPUT_PROBE_LAUNCH) {
         float px, py, pz, dx, dy, dz, E;
         launch_state(P, P.rt_tab, (uint32_t)idx, (uint32_t)x[i], px, py, pz, dx, dy, dz, E);

@@ -15,7 +15,8 @@ area (and the maps themselves) to the measurement.
   convex hull of a map's points (the area of a ternary library in the ternary
   diagram; a volume share for four elements).
 * ``diagnose_tilt`` estimates the common tilt of a measured map from maps
-  simulated at a range of tilts, by the area criterion and by least squares.
+  simulated at a range of tilts, by the area criterion and by least squares
+  with a fitted reference (``fit_tilt``).
 """
 
 from __future__ import annotations
@@ -94,18 +95,58 @@ def _parabola_min(x, y):
     return float(-b / (2 * a)) if a > 0 else float(x1)
 
 
+def _rescale(comp, log_k):
+    """Composition map with element j's arrivals scaled by exp(log_k[j]) (the effect of
+    another reference-patch count): c_j -> k_j c_j / sum_i k_i c_i, in at.%."""
+    a = np.asarray(comp, dtype=np.float64) * np.exp(np.asarray(log_k))[None, :]
+    return 100.0 * a / a.sum(axis=1, keepdims=True)
+
+
+def fit_tilt(measured, tilts, simulated):
+    """Least-squares tilt of a measured map with a fitted reference.
+
+    The simulated map at tilt t is interpolated linearly between the scan's
+    neighbouring tilts, and each element's arrivals get a free scale factor
+    (element 0's fixed), which absorbs the count noise of the single reference
+    patch that every composition is normalised to.  Minimises the mean squared
+    at.% difference over (t, log factors) from the best scanned tilt (scipy's
+    trust-region least squares); returns (tilt, factors, mse)."""
+    from scipy.optimize import least_squares
+
+    tilts = np.asarray(tilts, dtype=np.float64)
+    sim = np.asarray(simulated, dtype=np.float64)
+    meas = np.asarray(measured, dtype=np.float64)
+    n_el = meas.shape[1]
+
+    def model(t):
+        i = int(np.clip(np.searchsorted(tilts, t) - 1, 0, len(tilts) - 2))
+        f = (t - tilts[i]) / (tilts[i + 1] - tilts[i])
+        return (1.0 - f) * sim[i] + f * sim[i + 1]
+
+    def resid(x):
+        k = np.concatenate([[0.0], x[1:]])
+        return (_rescale(model(x[0]), k) - meas).ravel()
+
+    mse0 = ((sim - meas[None]) ** 2).mean(axis=(1, 2))
+    x0 = np.concatenate([[tilts[int(np.argmin(mse0))]], np.zeros(n_el - 1)])
+    lo = np.concatenate([[tilts[0]], np.full(n_el - 1, -0.5)])
+    hi = np.concatenate([[tilts[-1]], np.full(n_el - 1, 0.5)])
+    r = least_squares(resid, x0, bounds=(lo, hi), x_scale=np.concatenate([[1.0], np.full(n_el - 1, 0.01)]),
+                      xtol=1e-10, ftol=1e-12)
+    return float(r.x[0]), np.exp(np.concatenate([[0.0], r.x[1:]])), float(np.mean(r.fun ** 2))
+
+
 def diagnose_tilt(measured, tilts, simulated):
     """Common cathode tilt of a measured library map.
 
     measured: [n_points][n_el] at.%; simulated: [n_tilts][n_points][n_el] at.%
     at the increasing `tilts` (degrees).  Returns the tilt at which the
     simulated compositional area equals the measured one (linear interpolation
-    between the bracketing tilts; None when no bracket exists), the tilt of
-    least mean squared composition difference (parabola through the best
-    three), and the per-tilt areas and mean squared differences.  The area
-    criterion is the one the paper uses; the point-by-point least squares is
-    sensitive to the count noise of the reference patch, which moves a whole
-    map, and needs far more atoms for the same precision."""
+    between the bracketing tilts; None when no bracket exists; the criterion
+    the paper uses), the least-squares tilt with a fitted reference
+    (``fit_tilt``), the tilt of least mean squared difference of the maps as
+    they are (parabola through the best three, which the reference patch's
+    count noise shifts), and the per-tilt areas and mean squared differences."""
     tilts = np.asarray(tilts, dtype=np.float64)
     sim = np.asarray(simulated, dtype=np.float64)
     meas = np.asarray(measured, dtype=np.float64)
@@ -123,5 +164,7 @@ def diagnose_tilt(measured, tilts, simulated):
             break
     if t_area is None and areas[-1] == a_meas:
         t_area = float(tilts[-1])
-    return {"tilt_area": t_area, "tilt_lsq": _parabola_min(tilts, mse), "area_measured": a_meas,
-            "areas": areas.tolist(), "mse": mse.tolist()}
+    t_fit, factors, mse_fit = fit_tilt(meas, tilts, sim)
+    return {"tilt_area": t_area, "tilt_lsq": t_fit, "lsq_factors": factors.tolist(), "lsq_mse": mse_fit,
+            "tilt_lsq_raw": _parabola_min(tilts, mse), "area_measured": a_meas, "areas": areas.tolist(),
+            "mse": mse.tolist()}

@@ -224,3 +224,39 @@ def test_composition_map_matches_the_oracle(torch, pkg, oracle_mod):
     comp_o, _ = oracle_mod.composition(counts, patch, 0, rates, cal[:, 4], cal[:, 5])
     assert np.all(np.isfinite(comp_o)) and np.allclose(comp_o.sum(1), 100.0)
     assert np.max(np.abs(comp_gpu - comp_o)) < 0.1, np.abs(comp_gpu - comp_o)
+
+
+def test_inverse_solve_at_configuration(torch, pkg):
+    """The adjoint workload at its size: the quaternary scene at 1e7 atoms per cathode
+    per step, the 342-point map, Table S1 rate and voltage lines (power moves both the
+    rate and, through the discharge voltage, the Thompson cut-off).  The target map is
+    transported from random true (p, P) drawn inside Table 1's power ranges and
+    0.3-1 Pa, with its own seed; the fit starts at the ranges' midpoints and 0.5 Pa
+    and runs 50 Adam steps with a fixed seed of its own (common random numbers within
+    the fit, independent noise against the target).  Recovered: the pressure and the
+    power fractions (a common scale of all powers is only weakly determined)."""
+    from paper_2411_14413_gb300.adjoint import MapSetup, inverse_solve
+    from workloads.measurement import POWER_RANGE, voltage_points
+
+    rng = np.random.default_rng(20241122)
+    true_p = float(math.exp(rng.uniform(math.log(0.3), math.log(1.0))))
+    true_pw = np.array([rng.uniform(*POWER_RANGE[s]) for s in QUAT])
+    volt = []
+    for s in QUAT:
+        (q1, v1), (q2, v2) = voltage_points(s)
+        volt.append([q1, v1, q2, v2])
+    patch, pts, ref = measurement_patches()
+    assert patch.max() + 1 == 342
+    sc = workloads.scene_quaternary(n_per_cathode=10_000_000)
+    ms = MapSetup(sc, patch, ref, _calibration(), voltage=np.array(volt))
+    target = ms.forward(true_p, true_pw, seed=987654).clone()
+    start = np.array([0.5 * (POWER_RANGE[s][0] + POWER_RANGE[s][1]) for s in QUAT])
+    hist = inverse_solve(ms, target, math.log(0.5), start, steps=50, lr=0.1, seed=1)
+    ms.close()
+    frac = lambda x: np.asarray(x) / np.sum(x)
+    last = hist[-1]
+    print("C4 solve: true p", true_p, "fit p", last["p"], "true P", true_pw, "fit P", last["power"],
+          "loss", hist[0]["loss"], "->", last["loss"])
+    assert last["loss"] < 0.02 * hist[0]["loss"], (hist[0]["loss"], last["loss"])
+    assert abs(last["p"] / true_p - 1.0) < 0.1, (true_p, last["p"])
+    assert np.abs(frac(last["power"]) - frac(true_pw)).max() < 0.01, (true_pw, last["power"])

@@ -1,7 +1,7 @@
 """Tilt scan on the GPU: the maps of all tilts from one launch (checked against
 the oracle's composition arithmetic on the same counts), and the recovery of
-the tilt of a map simulated at a tilt between the scanned ones by the
-compositional-area criterion."""
+the tilt of a map simulated at a tilt between the scanned ones, by the
+compositional-area criterion and by least squares with a fitted reference."""
 
 import numpy as np
 import pytest
@@ -57,7 +57,8 @@ def test_tilt_scan_maps_and_diagnosis(pkg, oracle_mod):
           "areas", np.round(d["areas"], 5), "mse", np.round(d["mse"], 4))
     # a larger common tilt shrinks the covered compositional area, step by step
     assert all(a > b for a, b in zip(d["areas"], d["areas"][1:])), d["areas"]
-    assert d["tilt_area"] is not None and abs(d["tilt_area"] - true_tilt) < 0.75, d
-    # the point-by-point least-squares criterion is limited by the count noise of
-    # the reference patch (~0.2 at.% per map at 1e8 atoms): only a range check
-    assert tilts[0] <= d["tilt_lsq"] <= tilts[-1]
+    assert d["tilt_area"] is not None and abs(d["tilt_area"] - true_tilt) < 0.5, d
+    # point-by-point least squares with a fitted reference: per-element factors absorb
+    # the count noise of the reference patch that every map is normalised to
+    assert abs(d["tilt_lsq"] - true_tilt) < 0.5, d
+    assert np.all(np.abs(np.asarray(d["lsq_factors"]) - 1.0) < 0.05), d["lsq_factors"]

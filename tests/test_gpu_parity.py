@@ -70,6 +70,29 @@ def test_probe_chi_and_bmax(torch, pkg, oracle_mod):
     tr.close()
 
 
+def test_probe_collision_deflection(torch, pkg, oracle_mod):
+    """The deflection as a collision computes it from the impact-parameter uniform u
+    (b = b_max sqrt(u)): the device's deflection table inside its range (ln eps in
+    [-26, -4], ln(b/b_max) >= -6), the Gauss-Mehler integral outside, both against the
+    oracle's adaptive quadrature at the oracle's own b_max."""
+    sc = workloads.scene_single_ni(n=10)
+    tr = pkg.Transport(sc)
+    rng = np.random.default_rng(5)
+    le = np.concatenate([rng.uniform(-27.0, -3.0, 3000), np.linspace(-26.0, -4.0, 45)])
+    u = np.concatenate([rng.uniform(1e-7, 1.0, 3000), np.full(45, 1.0)])
+    u[::7] = np.exp(2 * rng.uniform(-7.0, 0.0, len(u[::7])))      # deep into small b, below the table
+    x = np.empty(2 * len(le))
+    x[0::2], x[1::2] = np.exp(le), u
+    got = tr.probe("chi_u", 0, x)
+    ref = np.array([oracle_mod.chi(math.exp(a), oracle_mod.bmax_interp(math.exp(a), CHI_MIN) * math.sqrt(w))
+                    for a, w in zip(le, u)])
+    err = np.abs(got - ref)
+    assert err.max() < 2e-6, (err.max(), le[err.argmax()], u[err.argmax()])
+    inside = (le >= -26.0) & (le < -4.0) & (0.5 * np.log(u) >= -6.0)
+    assert inside.sum() > 2000 and (~inside).sum() > 300
+    tr.close()
+
+
 @pytest.mark.parametrize("physics", [{}, {"interaction": "hard_sphere"}, {"gas_motion": "stationary"}])
 def test_probe_rate_tables(torch, pkg, oracle_mod, physics):
     sc = workloads.scene_quaternary(n_per_cathode=10, physics=physics)
@@ -89,9 +112,12 @@ def test_probe_rate_tables(torch, pkg, oracle_mod, physics):
         ok = Kr > 0
         assert np.max(np.abs(K[ok] / Kr[ok] - 1)) < 2e-5, (c, np.max(np.abs(K[ok] / Kr[ok] - 1)))
         if physics.get("gas_motion", "thermal") == "thermal":
-            M = tr.probe("M", c, v)
-            Mr = np.array([o.M(c, x) for x in v])
-            assert np.max(np.abs(M / Mr - 1)) < 2e-5
+            # the partner-rejection envelope (A, B) against the oracle's hull construction
+            AB = tr.probe("M", c, v).reshape(-1, 2)
+            ABr = np.array([o.envelope(c, x) for x in v])
+            scale = ABr[:, 0] + 1.6 * ABr[:, 1]            # the envelope's size at the mean |V|/s
+            assert np.max(np.abs(AB[:, 0] - ABr[:, 0]) / scale) < 2e-5, (c, np.abs(AB - ABr).max(0))
+            assert np.max(np.abs(AB[:, 1] - ABr[:, 1]) / scale) < 2e-5, (c, np.abs(AB - ABr).max(0))
     tr.close()
 
 

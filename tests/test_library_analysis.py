@@ -67,3 +67,31 @@ def test_diagnose_tilt_recovers_a_known_shrink():
     assert d["tilt_area"] == pytest.approx(30.6, abs=0.05)
     assert d["tilt_lsq"] == pytest.approx(30.6, abs=1e-6)
     assert all(a > b for a, b in zip(d["areas"], d["areas"][1:]))
+
+
+def test_fit_tilt_absorbs_reference_patch_scale():
+    """A measured map whose elements are rescaled (the effect of a noisy count in the
+    reference patch every map is normalised to): the least-squares fit with free
+    per-element factors returns the true tilt and the factors.  The tilt dependence
+    is a smooth rotation of the points around the centre, linear within a scan step."""
+    rng = np.random.default_rng(4)
+    base = rng.dirichlet([6, 6, 6], size=300) * 100 - 100 / 3
+
+    def lib(t):
+        a = math.radians(4.0 * (t - 30.0))
+        # rotate within the plane of compositions (rows keep summing to 100)
+        u = np.array([1.0, -1.0, 0.0]) / math.sqrt(2)
+        v = np.array([1.0, 1.0, -2.0]) / math.sqrt(6)
+        x, y = base @ u, base @ v
+        xr, yr = x * math.cos(a) - y * math.sin(a), x * math.sin(a) + y * math.cos(a)
+        return 100 / 3 + np.outer(xr, u) + np.outer(yr, v)
+
+    tilts = np.arange(26.0, 34.01, 0.25)
+    k_true = np.array([1.0, 1.006, 0.993])
+    meas = library._rescale(lib(30.6), np.log(k_true))
+    t, k, mse = library.fit_tilt(meas, tilts, [lib(x) for x in tilts])
+    assert t == pytest.approx(30.6, abs=2e-3)
+    assert np.allclose(k, k_true, rtol=2e-4)
+    assert mse < 1e-4
+    d = library.diagnose_tilt(meas, tilts, [lib(x) for x in tilts])
+    assert d["tilt_lsq"] == pytest.approx(30.6, abs=2e-3)
