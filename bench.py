@@ -33,6 +33,7 @@ workload (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -369,7 +370,7 @@ def run_ours(args, rank, world, local_rank):
     for k2, v in host.items():
         setattr(ht, k2, v.data_ptr())
     d2h = sum(v.numel() * v.element_size() for v in host.values())
-    h2d = len(sc.instances) * 40
+    h2d = len(sc.instances) * ctypes.sizeof(N.sput_instance)   # the instance table uploaded per step
     e2e_coll = 0
     e2e_t = 0.0
     if not args.no_e2e:

@@ -33,7 +33,8 @@
  *   a = 0.8853 a_0 (Z1^1/2 + Z2^1/2)^(-2/3).
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = (seed low
- * word, seed high word) and counter = (particle id, instance, event, block).
+ * word, seed high word) and counter = (particle id, stream, event, block), the
+ * stream being the instance index unless sput_instance.rng_stream sets it.
  * Event 0 is the launch (block 0: racetrack radius, racetrack azimuth, energy,
  * polar cosine; block 1 word 0: emission azimuth).  Event k >= 1 is flight k
  * (block 0: flight length, impact parameter, scattering azimuth; block 1+a,
@@ -67,7 +68,7 @@
 extern "C" {
 #endif
 
-#define SPUT_ABI_VERSION 4
+#define SPUT_ABI_VERSION 5
 
 typedef enum sput_status {
     SPUT_OK = 0,
@@ -151,6 +152,11 @@ typedef struct sput_instance {   /* one (cathode, process condition) pair */
     double E_i;                  /* incident ion energy, eV (set by the discharge voltage) */
     double k;                    /* head-on factor of the cut-off, 0.4 in the paper */
     uint64_t n_particles;        /* < 2^32 per instance */
+    uint32_t rng_stream;         /* word 1 of the Philox counter: 0 = the instance index; s > 0 = s - 1.
+                                    Instances with the same stream draw the same random numbers for the
+                                    same particle ids (common random numbers across conditions, e.g. the
+                                    tilts of a scan) */
+    uint32_t reserved;
 } sput_instance;
 
 typedef struct sput_grid {

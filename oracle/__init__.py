@@ -172,7 +172,7 @@ def _flatten(scene):
         cath[i, 21] = c["target"]
     inst = np.zeros((len(scene.instances), 8), float)
     for i, I in enumerate(scene.instances):
-        inst[i, 0:5] = [I["geometry"], I["cathode"], I["pressure"], I["E_i"], I["k"]]
+        inst[i, 0:6] = [I["geometry"], I["cathode"], I["pressure"], I["E_i"], I["k"], I.get("rng_stream", 0)]
     g = scene.grid
     grid = np.array([g["nx"], g["ny"], g["half_u"], g["half_v"], g["n_ebins"], g["e_hist_max"],
                      g["n_abins"], 0.0], float)

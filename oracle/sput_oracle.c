@@ -339,12 +339,20 @@ static void* bm_worker(void* arg)
 
 static const double* bmax_nodes(double chi_min)
 {
+    /* the last table this thread used, without taking the lock (tables are never freed) */
+    static __thread double tl_chi = -1.0;
+    static __thread const double* tl_node = NULL;
+    if (tl_node && tl_chi == chi_min) return tl_node;
+    const double* found = NULL;
     pthread_mutex_lock(&bm_mutex);
     for (int i = 0; i < bm_ncache; ++i)
-        if (bm_caches[i].chi_min == chi_min) {
-            pthread_mutex_unlock(&bm_mutex);
-            return bm_caches[i].node;
-        }
+        if (bm_caches[i].chi_min == chi_min) found = bm_caches[i].node;
+    if (found) {
+        pthread_mutex_unlock(&bm_mutex);
+        tl_chi = chi_min;
+        tl_node = found;
+        return found;
+    }
     double* node = (double*)malloc(sizeof(double) * BM_N);
     enum { NT = 16 };
     pthread_t th[NT];
@@ -362,6 +370,8 @@ static const double* bmax_nodes(double chi_min)
     bm_caches[slot].chi_min = chi_min;
     bm_caches[slot].node = node;
     pthread_mutex_unlock(&bm_mutex);
+    tl_chi = chi_min;
+    tl_node = node;
     return node;
 }
 
@@ -421,6 +431,7 @@ typedef struct {
     double pressure, E_i, k;
     double n_gas;   /* mm^-3 */
     double E_max;
+    uint32_t stream; /* word 1 of the Philox counters of the instance's particles */
 } inst_t;
 
 typedef struct or_scene {
@@ -975,7 +986,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
     const inst_t* I = &S->inst[ii];
     const cath_t* c = &S->cath[I->cathode];
     const geom_t* G = &S->geoms[I->geometry];
-    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, (uint32_t)ii};
+    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, S->inst[ii].stream};
     uint32_t w[4];
 
     /* launch: event 0 */
@@ -1095,7 +1106,7 @@ static void transport_one(const or_scene* S, uint64_t seed, int ii, uint64_t pid
  *   prims[16*n]     kind c[3] u[3] v[3] p0 p1 (rest unused)
  *   geoms[3*n] int  prim_begin prim_count substrate_local
  *   cath[32*n]      Z mass U_s c[3] n[3] e1[3] rt_r0 rt_sigma rt_R coef[6] target_local
- *   inst[8*n]       geometry cathode pressure E_i k
+ *   inst[8*n]       geometry cathode pressure E_i k rng_stream (0 = the instance index, s > 0 = s - 1)
  *   grid[8]         nx ny half_u half_v n_ebins e_hist_max n_abins
  *   phys[8]         chi_min(rad) interaction hs_diameter gas_motion max_attempts max_collisions
  */
@@ -1180,6 +1191,7 @@ or_scene* or_scene_new(const double* chamber, int n_prims, const double* prims, 
         I->pressure = q[2];
         I->E_i = q[3];
         I->k = q[4];
+        I->stream = q[5] > 0.0 ? (uint32_t)q[5] - 1u : (uint32_t)i;
         I->n_gas = I->pressure / (KB_J * S->T) * 1e-9; /* m^-3 -> mm^-3 */
         const cath_t* c = &S->cath[I->cathode];
         I->E_max = or_emax(I->k, S->gas_mass, c->mass, I->E_i, c->U_s);
@@ -1311,7 +1323,7 @@ void or_collide(const or_scene* S, int c, const double* v, const double* V, doub
 /* draw the gas partner of collision `event` for particle (inst, pid) */
 int or_partner(const or_scene* S, uint64_t seed, int inst, uint64_t pid, uint32_t event, const double* v, double* V)
 {
-    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, (uint32_t)inst};
+    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, S->inst[inst].stream};
     return sample_partner(S, &S->cath[S->inst[inst].cathode], &st, event, v, V);
 }
 
@@ -1320,7 +1332,7 @@ int or_partner(const or_scene* S, uint64_t seed, int inst, uint64_t pid, uint32_
 void or_thermalize(const or_scene* S, uint64_t seed, int inst, uint64_t pid, double E0, int n_coll, double* speeds)
 {
     const cath_t* c = &S->cath[S->inst[inst].cathode];
-    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, (uint32_t)inst};
+    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, S->inst[inst].stream};
     double v[3] = {0.0, 0.0, speed_of_E(E0, c->mass)};
     uint32_t w[4];
     for (int k = 1; k <= n_coll; ++k) {
@@ -1338,7 +1350,7 @@ void or_launch(const or_scene* S, uint64_t seed, int ii, uint64_t pid, double* p
 {
     const inst_t* I = &S->inst[ii];
     const cath_t* c = &S->cath[I->cathode];
-    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, (uint32_t)ii};
+    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, (uint32_t)pid, S->inst[ii].stream};
     uint32_t w[4];
     draw(&st, 0u, 0u, w);
     double r = or_racetrack_r(c->rt_r0, c->rt_sigma, c->rt_R, rn(w[0]));

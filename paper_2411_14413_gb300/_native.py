@@ -83,7 +83,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # --------------------------------------------------------------- ABI mirror
-SPUT_ABI_VERSION = 4
+SPUT_ABI_VERSION = 5
 SPUT_OK = 0
 STATUS_NAMES = {0: "SPUT_OK", 1: "SPUT_ERR_INVALID_ARG", 2: "SPUT_ERR_INVALID_SCENE", 3: "SPUT_ERR_CUDA",
                 4: "SPUT_ERR_TIMEOUT", 5: "SPUT_ERR_DEVICE_CHECK", 6: "SPUT_ERR_UNSUPPORTED", 7: "SPUT_ERR_NO_MEMORY"}
@@ -121,7 +121,7 @@ class sput_cathode(C.Structure):
 
 class sput_instance(C.Structure):
     _fields_ = [("geometry", C.c_int), ("cathode", C.c_int), ("pressure", C.c_double), ("E_i", C.c_double),
-                ("k", C.c_double), ("n_particles", C.c_uint64)]
+                ("k", C.c_double), ("n_particles", C.c_uint64), ("rng_stream", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class sput_grid(C.Structure):

@@ -92,6 +92,7 @@ def instance_array(scene):
         q = inst[i]
         q.geometry, q.cathode = I["geometry"], I["cathode"]
         q.pressure, q.E_i, q.k, q.n_particles = I["pressure"], I["E_i"], I["k"], int(I["n"])
+        q.rng_stream = int(I.get("rng_stream", 0))
     return inst
 
 

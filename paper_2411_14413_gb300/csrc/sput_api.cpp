@@ -284,6 +284,7 @@ static sput_status pack_instances(sput_scene* S)
         D.kLambda = (float)(I.k * 4.0 * S->chamber.gas_mass * C.mass /
                             ((S->chamber.gas_mass + C.mass) * (S->chamber.gas_mass + C.mass)));
         D.ticket_begin = S->prefix[i];
+        D.stream = I.rng_stream ? I.rng_stream - 1u : (uint32_t)i;
         S->prefix[i + 1] = S->prefix[i] + I.n_particles;
     }
     S->n_tickets = S->prefix.back();

@@ -120,7 +120,8 @@ struct alignas(16) DevInstance {
     float U_s;
     float kLambda;        // d E_max / d E_i = k Lambda
     unsigned long long ticket_begin;
-    unsigned long long pad2;
+    uint32_t stream;      // word 1 of every Philox counter of this instance's particles
+    uint32_t pad2;
 };
 
 // Everything the transport kernel needs; passed by value (kernel parameter).

@@ -101,7 +101,14 @@ struct TableView {
     int n_w;           // entries of w (bounds of the checked build)
     float bm_lo, bm_inv_h;
     unsigned int* status;
+    const uint32_t* stream;  // Philox stream word per instance (shared memory), or null: read P.inst
 };
+
+// word 1 of the Philox counters of instance `inst`'s particles
+__device__ __forceinline__ uint32_t stream_of(const TableView& T, const Params& P, uint32_t inst)
+{
+    return T.stream ? T.stream[inst] : P.inst[inst].stream;
+}
 
 __device__ __forceinline__ float bmax_eval(const TableView& T, float ln_eps)
 {
@@ -346,8 +353,8 @@ __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t ins
 {
     const DevInstance& I = P.inst[inst];
     const DevCathode& C = P.cath[I.cathode];
-    const uint4 w0 = philox(P.key0, P.key1, pid, inst, 0u, 0u);
-    const uint4 w1 = philox(P.key0, P.key1, pid, inst, 0u, 1u);
+    const uint4 w0 = philox(P.key0, P.key1, pid, I.stream, 0u, 0u);
+    const uint4 w1 = philox(P.key0, P.key1, pid, I.stream, 0u, 1u);
     const float r = racetrack_r(C, rt_tab, P.rt_n, P.n_rt_all, P.status, rn(w0.x));
     float sa, ca;
     sincospif(2.0f * rn(w0.y), &sa, &ca);
@@ -477,7 +484,7 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     out.attempts = 0;
     out.nonfinite = 0;
     out.prim = -1;
-    w = philox(P.key0, P.key1, S.pid, S.inst, S.k, 0u);
+    w = philox(P.key0, P.key1, S.pid, stream_of(T, P, S.inst), S.k, 0u);
     const DevPair pr = pairs[S.pair];
     // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
     const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
@@ -610,7 +617,7 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         bool acc = false;
         float cx = 0.0f, cy = 0.0f, cz = 0.0f;
         if (a < A) {
-            const uint4 wn = philox(P.key0, P.key1, o_pid, o_inst, o_k, 1u + (uint32_t)a);
+            const uint4 wn = philox(P.key0, P.key1, o_pid, stream_of(T, P, o_inst), o_k, 1u + (uint32_t)a);
             const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
             const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
             float s1, c1, s3, c3;
@@ -763,7 +770,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
 
 // ------------------------------------------------------------- kernel
 struct SmemLayout {
-    size_t prims, geoms, pairs, bm, w, prefix, xh, gm, counters, total;
+    size_t prims, geoms, pairs, bm, w, prefix, xh, gm, stream, counters, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -788,6 +795,8 @@ __host__ __device__ inline SmemLayout smem_layout(const Params& p)
     o = align16(o + sizeof(float) * (p.n_bm + 1));
     L.gm = o;
     o = align16(o + sizeof(float4) * (kGMHalf + kGMHalfLo));
+    L.stream = o;
+    o = align16(o + sizeof(uint32_t) * p.n_inst);
     L.counters = o;
     o = align16(o + (p.smem_counters ? sizeof(unsigned int) * (size_t)p.n_inst * (p.max_prims + 1) : 0));
     L.total = o;
@@ -817,6 +826,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     unsigned long long* s_prefix = reinterpret_cast<unsigned long long*>(smem + L.prefix);
     float* s_xh = reinterpret_cast<float*>(smem + L.xh);
     float4* s_gm = reinterpret_cast<float4*>(smem + L.gm);
+    uint32_t* s_stream = reinterpret_cast<uint32_t*>(smem + L.stream);
     unsigned int* s_cnt = reinterpret_cast<unsigned int*>(smem + L.counters);
 
     copy16(s_prims, P.prims, sizeof(DevPrim) * P.n_prims);
@@ -828,6 +838,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     copy16(s_xh, P.xh_tab, sizeof(float) * (P.n_bm + 1));
     if (threadIdx.x < kGMHalf) s_gm[threadIdx.x] = P.gm[threadIdx.x];
     else if (threadIdx.x < kGMHalf + kGMHalfLo) s_gm[threadIdx.x] = P.gm_lo[threadIdx.x - kGMHalf];
+    for (int i = threadIdx.x; i < P.n_inst; i += blockDim.x) s_stream[i] = P.inst[i].stream;
     const int n_cnt = P.smem_counters ? P.n_inst * (P.max_prims + 1) : 0;
     for (int i = threadIdx.x; i < n_cnt; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
@@ -843,6 +854,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     T.bm_lo = P.bm_lo;
     T.bm_inv_h = P.bm_inv_h;
     T.status = P.status;
+    T.stream = s_stream;
 
     const int lane = threadIdx.x & 31;
     const unsigned lane_lt = (1u << lane) - 1u;
@@ -1035,6 +1047,7 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
     T.bm_lo = P.bm_lo;
     T.bm_inv_h = P.bm_inv_h;
     T.status = P.status;
+    T.stream = nullptr;
     if (what == SPUT_PROBE_TRACE) {
         // state after each flight of particle x[i] of instance idx, kTraceRows rows of 10;
         // the flight step is warp-collective, so lanes past n take part without a particle

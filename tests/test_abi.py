@@ -56,7 +56,7 @@ int main(void) {
   O(sput_tune_result, cand_rate) O(sput_run_opts, flags)
   O(sput_scene_desc, chamber) O(sput_scene_desc, prims) O(sput_scene_desc, grid) O(sput_scene_desc, physics)
   O(sput_cathode, rt_r0) O(sput_cathode, cos_coef) O(sput_cathode, launch_table) O(sput_cathode, n_E)
-  O(sput_cathode, E_hi) O(sput_instance, n_particles) O(sput_grid, e_hist_max)
+  O(sput_cathode, E_hi) O(sput_instance, n_particles) O(sput_instance, rng_stream) O(sput_grid, e_hist_max)
   O(sput_physics, max_collisions) O(sput_physics, thermal_switch_eV) O(sput_run_opts, timeout_ms) O(sput_run_stats, kernel_ms)
   O(sput_tally_layout, n_tickets) O(sput_record, score) O(sput_tallies, score_T)
   return 0;

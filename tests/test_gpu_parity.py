@@ -285,3 +285,25 @@ def test_full_size_quaternary_sampled_parity(torch, pkg, oracle_mod):
     g = {"prim": rec[:, 0], "cell": rec[:, 1]}
     frac, bad, allowed = _cell_parity(g, o)
     assert bad <= allowed, (frac, bad, allowed)
+
+
+def test_rng_stream_common_random_numbers(torch, pkg, oracle_mod):
+    """Instances on the same Philox stream (sput_instance.rng_stream) with the same
+    conditions transport the same particle ids identically on the device, and the
+    device follows the oracle with the streams set."""
+    sc = workloads.scene_quaternary(n_per_cathode=2000)
+    sc.instances[2] = dict(sc.instances[0], rng_stream=1)
+    sc.instances[0] = dict(sc.instances[0], rng_stream=1)
+    sc.instances[3] = dict(sc.instances[3], rng_stream=7)
+    tr = pkg.Transport(sc, records=True)
+    tr.run()
+    g = tr.records()
+    counts = tr.t["counts"].cpu().numpy()
+    tr.close()
+    a, c = slice(0, 2000), slice(4000, 6000)
+    for k in ("prim", "cell", "ncoll"):
+        assert np.array_equal(g[k][a], g[k][c]), k
+    assert np.array_equal(counts[0], counts[2])
+    o = oracle_mod.OracleScene(sc).run_all()
+    frac, bad, allowed = _cell_parity(g, o)
+    assert bad <= allowed, (frac, bad, allowed)

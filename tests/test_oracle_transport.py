@@ -244,3 +244,24 @@ def test_trace_agrees_with_the_outcome(oracle_mod):
             # row r holds the collision point of flight r: row r-1 position + t * direction of row r-1
             step = tr[r - 1, :3] + tr[r, 9] * tr[r - 1, 3:6]
             assert np.allclose(step, tr[r, :3], atol=1e-9 * (1 + np.abs(step).max()))
+
+
+def test_rng_stream_gives_common_random_numbers(oracle_mod):
+    """sput_instance.rng_stream: 0 draws the instance's own stream (its index), s > 0 the
+    stream s - 1; two instances on the same stream and conditions transport the same
+    particle ids identically, and a different stream gives different trajectories."""
+    sc = workloads.scene_quaternary(n_per_cathode=300)
+    base = oracle_mod.OracleScene(sc).run_all()
+    # instance 2 on instance 0's stream with instance 0's cathode and geometry
+    sc2 = workloads.scene_quaternary(n_per_cathode=300)
+    sc2.instances[2] = dict(sc2.instances[0], rng_stream=1)
+    sc2.instances[0] = dict(sc2.instances[0], rng_stream=1)
+    sc2.instances[1] = dict(sc2.instances[1], rng_stream=2)     # its own index + 1: unchanged
+    o = oracle_mod.OracleScene(sc2).run_all()
+    a, b, c = slice(0, 300), slice(300, 600), slice(600, 900)
+    for k in ("prim", "cell", "ncoll"):
+        assert np.array_equal(o[k][a], base[k][a]) and np.array_equal(o[k][c], base[k][a])
+        assert np.array_equal(o[k][b], base[k][b])
+    assert np.array_equal(o["E"][c], base["E"][a])
+    # instance 3 left on its own stream differs from instance 0's particles
+    assert not np.array_equal(base["ncoll"][slice(900, 1200)], base["ncoll"][a])
