@@ -89,7 +89,7 @@ WORK_MODEL = {"philox_block": PHILOX_BLOCK_OPS, "flight": OPS_PER_FLIGHT, "prim_
 # kernel (ncu smsp__thread_inst_executed.sum / collisions of one launch, small
 # case of the workload); the issue share is reported beside the algorithmic
 # fraction.  None = no capture of the current build.
-EXEC_LANE_INSTR_PER_COLLISION = {"quaternary": 2334.0, "large": 4388.0}
+EXEC_LANE_INSTR_PER_COLLISION = {"quaternary": 2378.0, "large": 3361.0}
 # DRAM bytes (read + write) of one launch of the quaternary workload, from the
 # one-pass capture of the current kernel; None whenever the kernel changed
 # after the capture.

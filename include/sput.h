@@ -260,6 +260,12 @@ typedef struct sput_run_opts {
                                        boundary run of the derivative with respect to the Thompson cut-off,
                                        d E[f]/dE_max = p(E_max) (E[f | E = E_max] - E[f]),
                                        p(E_max) = 2 U_s / (E_max (E_max + U_s)); Thompson cathodes only */
+#define SPUT_RUN_NO_CELL_MASKS 16   /* surface test over every primitive, by a counted loop */
+#define SPUT_RUN_CELL_MASKS 32      /* surface test restricted by the cell masks: a flight of length <= h (2 h)
+                                       tests only the primitives whose bounding sphere meets the cells within 1
+                                       (2) of its start, h = the chamber's longest side / 32 (geometries of at
+                                       most 64 primitives).  Default: on when the largest geometry has more than
+                                       32 primitives.  Results are identical either way; only the speed differs */
 #define SPUT_RUN_INJECT_NONFINITE 8 /* failure-path test aid: particle 0 of every instance starts with a NaN
                                        speed; the kernel retires it as timed out, sets the non-finite bit of
                                        device_status and the call returns SPUT_ERR_DEVICE_CHECK (with stats) */

@@ -199,6 +199,8 @@ SPUT_RUN_NO_SMEM_COUNTERS = 1
 SPUT_RUN_SMEM_COUNTERS = 2
 SPUT_RUN_LAUNCH_AT_CUTOFF = 4
 SPUT_RUN_INJECT_NONFINITE = 8
+SPUT_RUN_NO_CELL_MASKS = 16
+SPUT_RUN_CELL_MASKS = 32
 
 ABI_STRUCTS = [sput_chamber, sput_primitive, sput_geometry, sput_cathode, sput_instance, sput_grid, sput_physics,
                sput_scene_desc, sput_record, sput_tallies, sput_tally_layout, sput_run_opts, sput_run_stats,

@@ -90,6 +90,10 @@ struct sput_scene {
     // packed host copies
     std::vector<DevPrim> dprims;
     std::vector<DevGeom> dgeoms;
+    // cell masks of the surface test (empty: a geometry has more than 64 primitives)
+    std::vector<unsigned long long> cell_masks;
+    double cell_lo[3] = {0, 0, 0}, cell_h = 0.0;
+    int cell_n[3] = {0, 0, 0};
     std::vector<DevCathode> dcath;
     std::vector<DevPair> dpairs;
     std::vector<DevInstance> dinst;
@@ -108,7 +112,7 @@ struct sput_scene {
     // device memory
     unsigned char* d_blob = nullptr;
     size_t off_prims = 0, off_geoms = 0, off_cath = 0, off_pairs = 0, off_inst = 0, off_prefix = 0, off_bm = 0,
-           off_xh = 0, off_w = 0, off_rt = 0, off_lt = 0, off_chi = 0, blob_bytes = 0;
+           off_xh = 0, off_w = 0, off_rt = 0, off_lt = 0, off_chi = 0, off_cell = 0, blob_bytes = 0;
     // run scratch (allocated on the first run): ticket counter, stats, status word
     unsigned long long* d_scratch = nullptr;
     unsigned long long* h_scratch = nullptr;  // pinned
@@ -291,6 +295,73 @@ static sput_status pack_instances(sput_scene* S)
     return SPUT_OK;
 }
 
+// Cell masks of the surface test.  A uniform grid of cubic cells (edge h, 32 along the
+// chamber's longest side) covers the chamber box.  For every geometry, cell c and
+// r = 1, 2, a 64-bit mask holds the local primitives that a flight of length at most
+// r h starting in c can reach: those whose bounding sphere meets the block of cells
+// within r of c (grown by a margin for FP32 rounding), and the chamber box when that
+// block touches a wall.  A flight that long cannot leave the block, so testing the
+// mask's primitives in ascending order finds the same nearest hit, with the same
+// tie-breaking, as testing every primitive.  Geometries of more than 64 primitives
+// leave the masks out (every flight tests every primitive).
+static void build_cell_masks(sput_scene* S)
+{
+    S->cell_masks.clear();
+    S->cell_h = 0.0;
+    for (const sput_geometry& g : S->geoms)
+        if (g.prim_count > 64) return;
+    double ext[3], emax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        S->cell_lo[a] = S->chamber.box_lo[a];
+        ext[a] = S->chamber.box_hi[a] - S->chamber.box_lo[a];
+        emax = std::max(emax, ext[a]);
+    }
+    const double h = emax / 32.0;
+    for (int a = 0; a < 3; ++a) S->cell_n[a] = std::max(1, std::min(32, (int)std::ceil(ext[a] / h - 1e-9)));
+    S->cell_h = h;
+    const int nx = S->cell_n[0], ny = S->cell_n[1], nz = S->cell_n[2];
+    const size_t ncell = (size_t)nx * ny * nz;
+    const double margin = 1e-3 * h + 1e-3;
+    S->cell_masks.assign(S->geoms.size() * ncell * 2, 0ull);
+    for (size_t g = 0; g < S->geoms.size(); ++g) {
+        const sput_geometry& G = S->geoms[g];
+        S->dgeoms[g].cell_base = (int)(g * ncell * 2);
+        for (int iz = 0; iz < nz; ++iz)
+            for (int iy = 0; iy < ny; ++iy)
+                for (int ix = 0; ix < nx; ++ix) {
+                    const int idx[3] = {ix, iy, iz};
+                    for (int r = 1; r <= 2; ++r) {
+                        double blo[3], bhi[3];
+                        bool wall = false;
+                        for (int a = 0; a < 3; ++a) {
+                            blo[a] = S->cell_lo[a] + (idx[a] - r) * h - margin;
+                            bhi[a] = S->cell_lo[a] + (idx[a] + 1 + r) * h + margin;
+                            if (idx[a] - r <= 0 || idx[a] + r >= S->cell_n[a] - 1) wall = true;
+                        }
+                        unsigned long long m = 0ull;
+                        for (int li = 0; li < G.prim_count; ++li) {
+                            const DevPrim& Q = S->dprims[G.prim_begin + li];
+                            bool in;
+                            if (Q.kind == SPUT_PRIM_BOX) {
+                                in = wall;
+                            } else {
+                                const double c[3] = {Q.bx, Q.by, Q.bz};
+                                double d2 = 0.0;
+                                for (int a = 0; a < 3; ++a) {
+                                    const double d = std::max(0.0, std::max(blo[a] - c[a], c[a] - bhi[a]));
+                                    d2 += d * d;
+                                }
+                                const double rr = (double)Q.br + margin;
+                                in = d2 <= rr * rr;
+                            }
+                            if (in) m |= 1ull << li;
+                        }
+                        S->cell_masks[(size_t)S->dgeoms[g].cell_base + 2 * (((size_t)iz * ny + iy) * nx + ix) + (r - 1)] = m;
+                    }
+                }
+    }
+}
+
 sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scene** out)
 {
     sput::NvtxRange nvtx("sput_scene_create");
@@ -369,9 +440,10 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->dgeoms.resize(S->geoms.size());
     S->max_prims = 0;
     for (size_t g = 0; g < S->geoms.size(); ++g) {
-        S->dgeoms[g] = DevGeom{S->geoms[g].prim_begin, S->geoms[g].prim_count, S->geoms[g].substrate, 0};
+        S->dgeoms[g] = DevGeom{S->geoms[g].prim_begin, S->geoms[g].prim_count, S->geoms[g].substrate, -1};
         S->max_prims = std::max(S->max_prims, S->geoms[g].prim_count);
     }
+    build_cell_masks(S);
 
     // interaction pairs (one per distinct cathode element) and their E range
     std::map<std::pair<int, double>, int> pair_of;
@@ -544,6 +616,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     S->off_lt = place(sizeof(float) * S->lt.size());
     const ChiTable* ct = hard ? nullptr : &chi_table(S->physics.chi_min);
     S->off_chi = place(ct ? sizeof(float4) * ct->cells.size() : 0);
+    S->off_cell = place(sizeof(unsigned long long) * S->cell_masks.size());
     S->blob_bytes = o;
     cudaError_t e = cudaMalloc(&S->d_blob, S->blob_bytes);
     if (e != cudaSuccess) {
@@ -566,6 +639,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     put(S->off_rt, S->rt.data(), sizeof(float4) * S->rt.size());
     put(S->off_lt, S->lt.data(), sizeof(float) * S->lt.size());
     if (ct) put(S->off_chi, ct->cells.data(), sizeof(float4) * ct->cells.size());
+    put(S->off_cell, S->cell_masks.data(), sizeof(unsigned long long) * S->cell_masks.size());
     e = cudaMemcpy(S->d_blob, h.data(), S->blob_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_scratch, 64);
     if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
@@ -589,6 +663,14 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.rt_tab = reinterpret_cast<const float4*>(S->d_blob + S->off_rt);
     p.lt_tab = reinterpret_cast<const float*>(S->d_blob + S->off_lt);
     p.chi_tab = ct ? reinterpret_cast<const float4*>(S->d_blob + S->off_chi) : nullptr;
+    p.cell_mask = S->cell_masks.empty() ? nullptr
+                                        : reinterpret_cast<const unsigned long long*>(S->d_blob + S->off_cell);
+    for (int a = 0; a < 3; ++a) {
+        p.cell_lo[a] = (float)S->cell_lo[a];
+        p.cell_n[a] = S->cell_n[a];
+    }
+    p.cell_h = (float)S->cell_h;
+    p.cell_inv_h = S->cell_h > 0.0 ? (float)(1.0 / S->cell_h) : 0.0f;
     p.n_prims = (int)S->dprims.size();
     p.n_geoms = (int)S->dgeoms.size();
     p.n_pairs = (int)S->dpairs.size();
@@ -736,7 +818,8 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     int chunk = opts->ticket_chunk ? opts->ticket_chunk : S->def_chunk;
     if (chunk < 1 || chunk > (1 << 20)) return fail(SPUT_ERR_INVALID_ARG, "ticket_chunk out of range");
     if (opts->flags &
-        ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS | SPUT_RUN_LAUNCH_AT_CUTOFF | SPUT_RUN_INJECT_NONFINITE))
+        ~(SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS | SPUT_RUN_LAUNCH_AT_CUTOFF | SPUT_RUN_INJECT_NONFINITE |
+          SPUT_RUN_NO_CELL_MASKS | SPUT_RUN_CELL_MASKS))
         return fail(SPUT_ERR_INVALID_ARG, "unknown flags");
     const int cutoff = opts->flags & SPUT_RUN_LAUNCH_AT_CUTOFF;
     const int fsm = opts->flags & (SPUT_RUN_NO_SMEM_COUNTERS | SPUT_RUN_SMEM_COUNTERS);
@@ -769,6 +852,10 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     p.smem_counters = (flags & SPUT_RUN_NO_SMEM_COUNTERS) ? 0 : S->smem_counters_fit;
     p.launch_at_cutoff = cutoff ? 1 : 0;
     p.inject_nonfinite = (opts->flags & SPUT_RUN_INJECT_NONFINITE) ? 1 : 0;
+    // the masked surface test pays where geometries have many primitives (see SPUT_RUN_CELL_MASKS)
+    const bool masks = (opts->flags & SPUT_RUN_CELL_MASKS) ||
+                       (!(opts->flags & SPUT_RUN_NO_CELL_MASKS) && S->max_prims > 32);
+    if (!masks) p.cell_mask = nullptr;
 
     const TallySizes sz = tally_sizes(S);
     if (!opts->accumulate) {

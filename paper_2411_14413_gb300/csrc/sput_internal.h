@@ -70,7 +70,8 @@ struct alignas(16) DevPrim {
 };
 
 struct alignas(16) DevGeom {
-    int begin, count, substrate, pad;
+    int begin, count, substrate;
+    int cell_base;  // offset of this geometry's cell masks in Params::cell_mask (-1: none)
 };
 
 struct alignas(16) DevCathode {
@@ -139,6 +140,12 @@ struct Params {
     const float4* rt_tab;              // racetrack inverse-CDF pieces (2 rt_n per cathode)
     const float* lt_tab;               // joint launch-table CDFs (see DevCathode::lt_off)
     const float4* chi_tab;             // deflection table: kChiCells cells of 4 float4 (null: hard spheres)
+    // cell masks of the surface test (null: off): per geometry and cell of a uniform grid over
+    // the chamber, the local primitives a flight of length <= h (word 0) or <= 2 h (word 1)
+    // starting in the cell can reach
+    const unsigned long long* cell_mask;
+    float cell_lo[3], cell_h, cell_inv_h;
+    int cell_n[3];
     int n_prims, n_geoms, n_pairs, n_inst;
     int n_bm, n_w_total;               // n_w_total: leading w_tab entries (K, M) staged in shared memory
     int n_w_all, n_rt_all, n_lt_all;   // entries of w_tab, rt_tab and lt_tab (bounds of the checked build)

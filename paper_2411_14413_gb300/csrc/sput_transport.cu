@@ -278,6 +278,7 @@ struct Lane {
     bool diff;     // thermalised: random walk of the diffusion shortcut
     uint32_t pid, inst, k, ncoll;
     int gbegin, gcount, gsub, target, pair;
+    int gcell;  // the geometry's cell-mask offset (-1: none)
     float ng14, E_per_v2;
     unsigned long long ticket;
 };
@@ -444,6 +445,7 @@ __device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, u
     S.gbegin = G.begin;
     S.gcount = G.count;
     S.gsub = G.substrate;
+    S.gcell = P.cell_mask ? G.cell_base : -1;
     S.target = C.target;
     S.pair = idx_ok(P.status, I.pair, P.n_pairs) ? I.pair : 0;
     S.ng14 = I.ng14;
@@ -476,7 +478,7 @@ struct StepOut {
 // pre-flight position and out.t is the hit distance.  Otherwise the atom moves
 // to the collision point; w is the flight's Philox block (words 1 and 2, the
 // impact parameter and azimuth, are used by the collision; word 3 is unused).
-template <int kMode>
+template <int kMode, bool kMasks>
 __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const DevPrim* prims, const DevPair* pairs,
                            StepOut& out, uint4& w)
 {
@@ -504,25 +506,61 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     }
 
     // surface test: nearest hit, ties to the lowest index; the emitting target
-    // is skipped on the first flight
+    // is skipped on the first flight.  Every primitive whose bounding sphere lies
+    // within min(ell, best t) is tested (margin covers FP32 rounding): no hit
+    // beyond that can be the landing.
     float tb = CUDART_INF_F;
     int hb = -1;
     const int excl = S.k == 1u ? S.target : -1;
-    for (int li = 0; li < S.gcount; ++li) {
-        if (li == excl) continue;
-        if (!idx_ok(P.status, S.gbegin + li, P.n_prims)) break;
-        const DevPrim& Q = prims[S.gbegin + li];
-        // skip a primitive whose bounding sphere lies beyond min(ell, best t): no
-        // hit on it can be the landing (margin covers FP32 rounding)
-        if (Q.kind != SPUT_PRIM_BOX) {
-            const float ex = Q.bx - S.px, ey = Q.by - S.py, ez = Q.bz - S.pz;
-            const float reach = fminf(ell, tb) * 1.0001f + Q.br + 1e-3f;
-            if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
+    if (!kMasks) {
+        for (int li = 0; li < S.gcount; ++li) {
+            if (li == excl) continue;
+            if (!idx_ok(P.status, S.gbegin + li, P.n_prims)) break;
+            const DevPrim& Q = prims[S.gbegin + li];
+            if (Q.kind != SPUT_PRIM_BOX) {
+                const float ex = Q.bx - S.px, ey = Q.by - S.py, ez = Q.bz - S.pz;
+                const float reach = fminf(ell, tb) * 1.0001f + Q.br + 1e-3f;
+                if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
+            }
+            const float t = hit_prim(Q, P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
+            if (t < tb) {
+                tb = t;
+                hb = li;
+            }
         }
-        const float t = hit_prim(Q, P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
-        if (t < tb) {
-            tb = t;
-            hb = li;
+    } else {
+        // candidates as 32-bit masks of local indices, visited in ascending order; a
+        // flight of length <= h (2 h) takes its cell's mask of the primitives it can
+        // reach, which leaves the result unchanged
+        unsigned long long near = ~0ull;
+        if (ell <= 2.0f * P.cell_h) {
+            const int ix = min(max((int)floorf((S.px - P.cell_lo[0]) * P.cell_inv_h), 0), P.cell_n[0] - 1);
+            const int iy = min(max((int)floorf((S.py - P.cell_lo[1]) * P.cell_inv_h), 0), P.cell_n[1] - 1);
+            const int iz = min(max((int)floorf((S.pz - P.cell_lo[2]) * P.cell_inv_h), 0), P.cell_n[2] - 1);
+            const int c = (iz * P.cell_n[1] + iy) * P.cell_n[0] + ix;
+            near = __ldg(P.cell_mask + S.gcell + 2 * c + (ell <= P.cell_h ? 0 : 1));
+        }
+        for (int base = 0; base < S.gcount; base += 32) {
+            const int left = S.gcount - base;
+            unsigned mask = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+            if (base < 64) mask &= (unsigned)(near >> base);
+            if (excl >= base && excl < base + 32) mask &= ~(1u << (excl - base));
+            while (mask) {
+                const int li = base + __ffs(mask) - 1;
+                mask &= mask - 1u;
+                if (!idx_ok(P.status, S.gbegin + li, P.n_prims)) break;
+                const DevPrim& Q = prims[S.gbegin + li];
+                if (Q.kind != SPUT_PRIM_BOX) {
+                    const float ex = Q.bx - S.px, ey = Q.by - S.py, ez = Q.bz - S.pz;
+                    const float reach = fminf(ell, tb) * 1.0001f + Q.br + 1e-3f;
+                    if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
+                }
+                const float t = hit_prim(Q, P, S.px, S.py, S.pz, S.dx, S.dy, S.dz);
+                if (t < tb) {
+                    tb = t;
+                    hb = li;
+                }
+            }
         }
     }
     if (hb >= 0 && tb <= ell) {
@@ -709,12 +747,21 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
         const float nvx = pr.m1M * vx + pr.m2M * Vx + pr.m2M * gpx;
         const float nvy = pr.m1M * vy + pr.m2M * Vy + pr.m2M * gpy;
         const float nvz = pr.m1M * vz + pr.m2M * Vz + pr.m2M * gpz;
-        const float sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
-        S.speed = sqrtf(sp2);
-        const float is = 1.0f / S.speed;
-        S.dx = nvx * is;
-        S.dy = nvy * is;
-        S.dz = nvz * is;
+        // an atom slowed to ~1e-15 km/s or below (gas at rest) would underflow the
+        // squares: scale by the exact power of two 2^60 first
+        const float up = nvx * nvx + nvy * nvy + nvz * nvz < 1e-30f ? 0x1p60f : 1.0f;
+        const float ux = nvx * up, uy = nvy * up, uz = nvz * up;
+        const float sp2 = ux * ux + uy * uy + uz * uz;
+        if (sp2 > 0.0f) {
+            const float sn = sqrtf(sp2);
+            const float is = 1.0f / sn;
+            S.speed = sn * (1.0f / up);
+            S.dx = ux * is;
+            S.dy = uy * is;
+            S.dz = uz * is;
+        } else {
+            S.speed = 0.0f;  // at rest: the direction is kept
+        }
     }
     ++S.ncoll;
 }
@@ -722,7 +769,7 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
 // One flight of every active lane of the warp (flight, surface test, then for
 // the lanes that collide: warp-wide partner sampling and the scattering).
 // Must be called by all 32 lanes together; inactive lanes return kStepNone.
-template <int kMode>
+template <int kMode, bool kMasks>
 __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const TableView& T, const DevPrim* prims,
                                 const DevPair* pairs, StepOut& out)
 {
@@ -731,7 +778,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
     out.attempts = 0;
     constexpr bool kScoreT = kMode == kModeScoreT;
     if (kScoreT) out.Gv = 0.0f;
-    if (active) res = flight_move<kMode>(S, P, T, prims, pairs, out, w);
+    if (active) res = flight_move<kMode, kMasks>(S, P, T, prims, pairs, out, w);
     // a thermalised atom (diffusion shortcut) turns isotropically at the end of its step
     const bool walk = kMode == kModeWalk && res == kStepCollided && S.diff;
     const bool coll = res == kStepCollided && !walk;
@@ -813,7 +860,7 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
     for (size_t i = (bytes / 16) * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
 }
 
-template <bool kCount64, int kMode>
+template <bool kCount64, int kMode, bool kMasks>
 __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -864,6 +911,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = S.scoreT = 0.0f;
     S.pid = S.inst = S.k = S.ncoll = 0u;
     S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
+    S.gcell = -1;
     S.ng14 = S.E_per_v2 = 0.0f;
     S.ticket = 0ull;
     bool alive = false;
@@ -915,7 +963,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
 
         // ---------------------------------------------------- one flight (all lanes together)
         StepOut so;
-        const int res = flight_step_warp<kMode>(alive, S, P, T, s_prims, s_pairs, so);
+        const int res = flight_step_warp<kMode, kMasks>(alive, S, P, T, s_prims, s_pairs, so);
         if (alive) ++c_flights;
         c_att += so.attempts;
         if (res == kStepLanded) {
@@ -1071,8 +1119,10 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
             if (!__any_sync(kFull, running)) break;
             StepOut so;
             const int status = P.E_switch > 0.0f
-                                   ? flight_step_warp<kModeWalk>(running, S, P, T, P.prims, P.pairs, so)
-                                   : flight_step_warp<kModePlain>(running, S, P, T, P.prims, P.pairs, so);
+                                   ? (P.cell_mask ? flight_step_warp<kModeWalk, true>(running, S, P, T, P.prims, P.pairs, so)
+                                                  : flight_step_warp<kModeWalk, false>(running, S, P, T, P.prims, P.pairs, so))
+                                   : (P.cell_mask ? flight_step_warp<kModePlain, true>(running, S, P, T, P.prims, P.pairs, so)
+                                                  : flight_step_warp<kModePlain, false>(running, S, P, T, P.prims, P.pairs, so));
             if (running) {
                 double* q = o + (size_t)r * 10;
                 float px = S.px, py = S.py, pz = S.pz;
@@ -1136,53 +1186,56 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
 
 size_t transport_smem_bytes(const Params& p) { return smem_layout(p).total; }
 
+namespace {
+
+using KernelFn = void (*)(const Params);
+
+// the instances [count type][mode][surface-test loop]
+KernelFn kernel_for(int count64, int mode, int masks)
+{
+    static const KernelFn tab[2][3][2] = {
+        {{transport_kernel<false, kModePlain, false>, transport_kernel<false, kModePlain, true>},
+         {transport_kernel<false, kModeScoreT, false>, transport_kernel<false, kModeScoreT, true>},
+         {transport_kernel<false, kModeWalk, false>, transport_kernel<false, kModeWalk, true>}},
+        {{transport_kernel<true, kModePlain, false>, transport_kernel<true, kModePlain, true>},
+         {transport_kernel<true, kModeScoreT, false>, transport_kernel<true, kModeScoreT, true>},
+         {transport_kernel<true, kModeWalk, false>, transport_kernel<true, kModeWalk, true>}}};
+    return tab[count64 ? 1 : 0][mode][masks ? 1 : 0];
+}
+
+}  // namespace
+
 int transport_max_blocks_per_sm(int count64, int threads, size_t smem)
 {
-    // the smallest occupancy of the three instances of this count type
-    int nb[3] = {0, 0, 0};
-    cudaError_t e[3];
-    if (count64) {
-        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], transport_kernel<true, kModePlain>, threads, smem);
-        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], transport_kernel<true, kModeScoreT>, threads, smem);
-        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], transport_kernel<true, kModeWalk>, threads, smem);
-    } else {
-        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], transport_kernel<false, kModePlain>, threads, smem);
-        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], transport_kernel<false, kModeScoreT>, threads, smem);
-        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], transport_kernel<false, kModeWalk>, threads, smem);
-    }
-    int m = nb[0];
-    for (int i = 0; i < 3; ++i) {
-        if (e[i] != cudaSuccess) return 0;
-        m = nb[i] < m ? nb[i] : m;
-    }
+    // the smallest occupancy of the instances of this count type
+    int m = 1 << 30;
+    for (int mode = 0; mode < 3; ++mode)
+        for (int masks = 0; masks < 2; ++masks) {
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(count64, mode, masks), threads, smem) !=
+                cudaSuccess)
+                return 0;
+            m = nb < m ? nb : m;
+        }
     return m;
 }
 
 int transport_configure(int max_dynamic_smem)
 {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(transport_kernel<true, kModePlain>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, kModePlain>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<true, kModeScoreT>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, kModeScoreT>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<true, kModeWalk>, a, max_dynamic_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(transport_kernel<false, kModeWalk>, a, max_dynamic_smem);
-    return (int)e;
+    for (int c64 = 0; c64 < 2; ++c64)
+        for (int mode = 0; mode < 3; ++mode)
+            for (int masks = 0; masks < 2; ++masks) {
+                const cudaError_t e = cudaFuncSetAttribute(kernel_for(c64, mode, masks), a, max_dynamic_smem);
+                if (e != cudaSuccess) return (int)e;
+            }
+    return 0;
 }
 
 int transport_launch(const Params& p, int count64, int blocks, int threads, size_t smem, void* stream)
 {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (p.score_T) {
-        if (count64) transport_kernel<true, kModeScoreT><<<blocks, threads, smem, s>>>(p);
-        else transport_kernel<false, kModeScoreT><<<blocks, threads, smem, s>>>(p);
-    } else if (p.E_switch > 0.0f) {
-        if (count64) transport_kernel<true, kModeWalk><<<blocks, threads, smem, s>>>(p);
-        else transport_kernel<false, kModeWalk><<<blocks, threads, smem, s>>>(p);
-    } else {
-        if (count64) transport_kernel<true, kModePlain><<<blocks, threads, smem, s>>>(p);
-        else transport_kernel<false, kModePlain><<<blocks, threads, smem, s>>>(p);
-    }
+    const int mode = p.score_T ? kModeScoreT : (p.E_switch > 0.0f ? kModeWalk : kModePlain);
+    kernel_for(count64, mode, p.cell_mask != nullptr)<<<blocks, threads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(p);
     return (int)cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ area (and the maps themselves) to the measurement.
   diagram; a volume share for four elements).
 * ``diagnose_tilt`` estimates the common tilt of a measured map from maps
   simulated at a range of tilts, by the area criterion and by least squares
-  with a fitted reference (``fit_tilt``).
+  with a fitted reference per simulated map (``fit_tilt``).
 """
 
 from __future__ import annotations
@@ -102,38 +102,40 @@ def _rescale(comp, log_k):
     return 100.0 * a / a.sum(axis=1, keepdims=True)
 
 
-def fit_tilt(measured, tilts, simulated):
-    """Least-squares tilt of a measured map with a fitted reference.
-
-    The simulated map at tilt t is interpolated linearly between the scan's
-    neighbouring tilts, and each element's arrivals get a free scale factor
-    (element 0's fixed), which absorbs the count noise of the single reference
-    patch that every composition is normalised to.  Minimises the mean squared
-    at.% difference over (t, log factors) from the best scanned tilt (scipy's
-    trust-region least squares); returns (tilt, factors, mse)."""
+def fit_reference(sim, measured):
+    """Per-element scale factors (element 0's fixed) of a simulated map that minimise its
+    mean squared at.% difference to the measured map, and that difference.  The factors
+    stand for the reference patch's counts, which every composition is normalised to and
+    whose count noise rescales each element's whole map."""
     from scipy.optimize import least_squares
 
-    tilts = np.asarray(tilts, dtype=np.float64)
-    sim = np.asarray(simulated, dtype=np.float64)
+    sim = np.asarray(sim, dtype=np.float64)
     meas = np.asarray(measured, dtype=np.float64)
     n_el = meas.shape[1]
 
-    def model(t):
-        i = int(np.clip(np.searchsorted(tilts, t) - 1, 0, len(tilts) - 2))
-        f = (t - tilts[i]) / (tilts[i + 1] - tilts[i])
-        return (1.0 - f) * sim[i] + f * sim[i + 1]
-
     def resid(x):
-        k = np.concatenate([[0.0], x[1:]])
-        return (_rescale(model(x[0]), k) - meas).ravel()
+        return (_rescale(sim, np.concatenate([[0.0], x])) - meas).ravel()
 
-    mse0 = ((sim - meas[None]) ** 2).mean(axis=(1, 2))
-    x0 = np.concatenate([[tilts[int(np.argmin(mse0))]], np.zeros(n_el - 1)])
-    lo = np.concatenate([[tilts[0]], np.full(n_el - 1, -0.5)])
-    hi = np.concatenate([[tilts[-1]], np.full(n_el - 1, 0.5)])
-    r = least_squares(resid, x0, bounds=(lo, hi), x_scale=np.concatenate([[1.0], np.full(n_el - 1, 0.01)]),
-                      xtol=1e-10, ftol=1e-12)
-    return float(r.x[0]), np.exp(np.concatenate([[0.0], r.x[1:]])), float(np.mean(r.fun ** 2))
+    r = least_squares(resid, np.zeros(n_el - 1), x_scale=0.01, xtol=1e-12, ftol=1e-14)
+    return np.exp(np.concatenate([[0.0], r.x])), float(np.mean(r.fun ** 2))
+
+
+def fit_tilt(measured, tilts, simulated):
+    """Least-squares tilt of a measured map with a fitted reference.
+
+    Every simulated map gets its own reference factors (``fit_reference``), so neither the
+    measured map's nor the simulated maps' reference-patch noise moves the estimate; the
+    tilt is the minimum of the quadratic fitted, over all scanned tilts, to these
+    mean squared differences (the scan's best tilt when the fit is not convex).
+    Returns (tilt, the factors at the scanned tilt nearest to it, the per-tilt
+    mean squared differences)."""
+    tilts = np.asarray(tilts, dtype=np.float64)
+    fits = [fit_reference(s, measured) for s in simulated]
+    mse = np.array([f[1] for f in fits])
+    c = np.polyfit(tilts, mse, 2)
+    t = float(-c[1] / (2.0 * c[0])) if c[0] > 0 else float(tilts[int(np.argmin(mse))])
+    t = float(np.clip(t, tilts[0], tilts[-1]))
+    return t, fits[int(np.argmin(np.abs(tilts - t)))][0], mse
 
 
 def diagnose_tilt(measured, tilts, simulated):
@@ -165,6 +167,6 @@ def diagnose_tilt(measured, tilts, simulated):
     if t_area is None and areas[-1] == a_meas:
         t_area = float(tilts[-1])
     t_fit, factors, mse_fit = fit_tilt(meas, tilts, sim)
-    return {"tilt_area": t_area, "tilt_lsq": t_fit, "lsq_factors": factors.tolist(), "lsq_mse": mse_fit,
+    return {"tilt_area": t_area, "tilt_lsq": t_fit, "lsq_factors": factors.tolist(), "lsq_mse": mse_fit.tolist(),
             "tilt_lsq_raw": _parabola_min(tilts, mse), "area_measured": a_meas, "areas": areas.tolist(),
             "mse": mse.tolist()}

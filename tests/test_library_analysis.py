@@ -65,7 +65,7 @@ def test_diagnose_tilt_recovers_a_known_shrink():
     tilts = np.arange(26.0, 34.01, 1.0)
     d = library.diagnose_tilt(lib(30.6), tilts, [lib(t) for t in tilts])
     assert d["tilt_area"] == pytest.approx(30.6, abs=0.05)
-    assert d["tilt_lsq"] == pytest.approx(30.6, abs=1e-6)
+    assert d["tilt_lsq"] == pytest.approx(30.6, abs=1e-3)   # per-map factors fitted numerically
     assert all(a > b for a, b in zip(d["areas"], d["areas"][1:]))
 
 
@@ -86,12 +86,17 @@ def test_fit_tilt_absorbs_reference_patch_scale():
         xr, yr = x * math.cos(a) - y * math.sin(a), x * math.sin(a) + y * math.cos(a)
         return 100 / 3 + np.outer(xr, u) + np.outer(yr, v)
 
-    tilts = np.arange(26.0, 34.01, 0.25)
+    tilts = np.arange(28.0, 33.01, 0.5)
     k_true = np.array([1.0, 1.006, 0.993])
-    meas = library._rescale(lib(30.6), np.log(k_true))
-    t, k, mse = library.fit_tilt(meas, tilts, [lib(x) for x in tilts])
-    assert t == pytest.approx(30.6, abs=2e-3)
-    assert np.allclose(k, k_true, rtol=2e-4)
-    assert mse < 1e-4
-    d = library.diagnose_tilt(meas, tilts, [lib(x) for x in tilts])
-    assert d["tilt_lsq"] == pytest.approx(30.6, abs=2e-3)
+    meas = library._rescale(lib(30.5), np.log(k_true))
+    # every simulated map with its own reference error: the per-map factors absorb them
+    rng = np.random.default_rng(9)
+    sims = [library._rescale(lib(x), rng.normal(0.0, 0.005, 3)) for x in tilts]
+    t, k, mse = library.fit_tilt(meas, tilts, sims)
+    assert t == pytest.approx(30.5, abs=0.02)
+    assert np.min(mse) < 1e-3
+    d = library.diagnose_tilt(meas, tilts, sims)
+    assert d["tilt_lsq"] == pytest.approx(30.5, abs=0.02)
+    # a single map's factors recover the measured map's reference error exactly
+    k1, m1 = library.fit_reference(lib(30.5), meas)
+    assert np.allclose(k1, k_true, rtol=1e-6) and m1 < 1e-12

@@ -315,10 +315,10 @@ def scene_tilt_pressure_sweep(n_range=(100_000, 10_000_000), n_pressures=16, n_t
 # count tallies of one tilt are contiguous; 200x200 int64 counts per instance.
 # ---------------------------------------------------------------------------
 def scene_tilt_scan(tilts, elements=("Pd", "Pt", "Ru"), n_per_cathode=1_000_000, pressure=0.5, T=300.0,
-                    E_i=400.0, nx=200, ny=200, physics=None, seed=0, common_random_numbers=True) -> Scene:
+                    E_i=400.0, nx=200, ny=200, physics=None, seed=0, common_random_numbers=False) -> Scene:
     """One library at several common tilts, tilt-major (len(elements) instances per tilt).
     With common_random_numbers every tilt's instance of an element draws that element's
-    random stream, so neighbouring tilts differ by the tilt rather than by noise."""
+    random stream (the same particle ids and random numbers at every tilt)."""
     box_lo, box_hi = (-200.0, -200.0, -100.0), (200.0, 200.0, 200.0)
     ta30 = math.radians(30.0)
     radial, zc = 120.0 * math.sin(ta30), 100.0 - 120.0 * math.cos(ta30)
