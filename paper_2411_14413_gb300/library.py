@@ -17,6 +17,13 @@ area (and the maps themselves) to the measurement.
 * ``diagnose_tilt`` estimates the common tilt of a measured map from maps
   simulated at a range of tilts, by the area criterion and by least squares
   with a fitted reference per simulated map (``fit_tilt``).
+* ``fit_tilt_newton`` refines the tilt by Newton steps on the fitted-reference
+  loss.  Its slope comes from the composition stage's adjoint
+  (``sput_composition_backward``: dL/dcomposition -> dL/dcounts) contracted
+  with the count derivative in tilt, a central difference of common random
+  numbers across the tilt instances (t - h, t, t + h) of one batched launch
+  (``TiltAdjoint``).  The tilt moves surfaces (the launch support itself), so
+  the transport's likelihood-ratio score does not give that count derivative.
 """
 
 from __future__ import annotations
@@ -35,6 +42,12 @@ def composition_maps(transport, n_el, patch_of_cell, ref_point, calibration, pow
 
     calibration: host [n_el][6] rate-line rows (P_a, R_a, P_b, R_b, density, mass)
     shared by every library; power: host [n_el] in W."""
+    return _composition_maps(transport, n_el, patch_of_cell, ref_point, calibration, power, seed, stream)[0]
+
+
+def _composition_maps(transport, n_el, patch_of_cell, ref_point, calibration, power, seed, stream):
+    """composition_maps, also returning the forward's patch counts [n_lib][n_el][n_points]
+    and the device patch map (both needed by the composition backward)."""
     import torch
 
     L = transport.layout
@@ -62,7 +75,7 @@ def composition_maps(transport, n_el, patch_of_cell, ref_point, calibration, pow
                                   pw.ctypes.data_as(C.c_void_p), C.c_void_p(patch_counts[t].data_ptr()),
                                   C.c_void_p(comp[t].data_ptr()), C.c_void_p(s))
         N.check(rc, "sput_composition")
-    return comp
+    return comp, patch_counts, patch
 
 
 def compositional_area(comp):
@@ -170,3 +183,128 @@ def diagnose_tilt(measured, tilts, simulated):
     return {"tilt_area": t_area, "tilt_lsq": t_fit, "lsq_factors": factors.tolist(), "lsq_mse": mse_fit.tolist(),
             "tilt_lsq_raw": _parabola_min(tilts, mse), "area_measured": a_meas, "areas": areas.tolist(),
             "mse": mse.tolist()}
+
+
+def fitted_loss_grad(sim, measured):
+    """Fitted-reference loss of a simulated map and its gradient in the map.
+
+    L(sim) = min_k mean((R(sim, k) - measured)^2) with R the per-element rescale
+    (``fit_reference``).  At the optimal factors k* the derivative of the minimum
+    is the partial derivative at fixed k* (the factors are stationary there):
+    with a = sim k*, S = sum_j a_j, R_j = 100 a_j / S and g = dL/dR,
+    dL/dsim_l = (k*_l / S) (100 g_l - sum_j g_j R_j), row by row.
+    Returns (L, k*, dL/dsim as [n_points][n_el])."""
+    sim = np.asarray(sim, dtype=np.float64)
+    meas = np.asarray(measured, dtype=np.float64)
+    k, loss = fit_reference(sim, meas)
+    a = sim * k[None, :]
+    S = a.sum(axis=1, keepdims=True)
+    R = 100.0 * a / S
+    g = 2.0 * (R - meas) / R.size
+    grad = (k[None, :] / S) * (100.0 * g - (g * R).sum(axis=1, keepdims=True))
+    return loss, k, grad
+
+
+class TiltAdjoint:
+    """Fitted-reference loss of a measured map at a common tilt t, with its slope and
+    curvature in t, from ONE batched launch of the library at tilts (t - h, t, t + h).
+
+    make_scene(tilts) must return a tilt-major scene of n_el instances per tilt in
+    which every tilt's instance of an element draws the same random stream (common
+    random numbers, e.g. ``workloads.scene_tilt_scan(..., common_random_numbers=True)``).
+    evaluate(t, h) returns
+      loss:  the fitted-reference loss at t (``fitted_loss_grad``);
+      slope: dL/dt, the adjoint of the composition stage at t (dL/dcomposition
+             -> dL/dcounts, ``sput_composition_backward``) contracted with the
+             central difference of the counts, (counts(t + h) - counts(t - h)) / 2h;
+      curv:  (L(t + h) - 2 L(t) + L(t - h)) / h^2 from the three fitted losses;
+      factors: the reference factors at t."""
+
+    def __init__(self, make_scene, measured, patch_of_cell, ref_point, calibration, power, seed=0, device=0):
+        self.make_scene = make_scene
+        self.measured = np.asarray(measured, dtype=np.float64)
+        self.patch_of_cell = np.ascontiguousarray(patch_of_cell, np.int32)
+        self.ref = int(ref_point)
+        self.n_el = self.measured.shape[1]
+        self.cal = np.ascontiguousarray(calibration, dtype=np.float64).reshape(self.n_el, 6)
+        self.power = np.ascontiguousarray(power, dtype=np.float64).reshape(self.n_el)
+        self.seed = seed
+        self.device = device
+        self.launches = 0
+
+    def evaluate(self, t, h):
+        import torch
+
+        from . import api
+
+        sc = self.make_scene([t - h, t, t + h])
+        if len(sc.instances) != 3 * self.n_el:
+            raise ValueError("the scene must hold n_el instances at each of the three tilts")
+        tr = api.Transport(sc, device=self.device, energy=False, prim_counts=False)
+        try:
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            comp, patch_counts, patch = _composition_maps(tr, self.n_el, self.patch_of_cell, self.ref, self.cal,
+                                                          self.power, self.seed, s)
+            self.launches += 1
+            comp_h = comp.cpu().numpy()
+            L_m = fit_reference(comp_h[0], self.measured)[1]
+            L_p = fit_reference(comp_h[2], self.measured)[1]
+            loss, k, grad = fitted_loss_grad(comp_h[1], self.measured)
+            dev = comp.device
+            n_cells = tr.layout.nx * tr.layout.ny
+            n_points = comp.shape[1]
+            g_comp = torch.as_tensor(np.ascontiguousarray(grad), dtype=torch.float64, device=dev)
+            g_patch = torch.empty((self.n_el, n_points), dtype=torch.float64, device=dev)
+            g_counts = torch.empty((self.n_el, n_cells), dtype=torch.float64, device=dev)
+            g_power = torch.empty(self.n_el, dtype=torch.float64, device=dev)
+            rc = N.load().sput_composition_backward(
+                self.n_el, n_cells, n_points, C.c_void_p(patch_counts[1].data_ptr()), C.c_void_p(patch.data_ptr()),
+                self.ref, self.cal.ctypes.data_as(C.c_void_p), self.power.ctypes.data_as(C.c_void_p),
+                C.c_void_p(g_comp.data_ptr()), C.c_void_p(g_patch.data_ptr()), C.c_void_p(g_counts.data_ptr()),
+                C.c_void_p(g_power.data_ptr()), C.c_void_p(s))
+            N.check(rc, "sput_composition_backward")
+            counts = tr.t["counts"].reshape(3, self.n_el, n_cells)
+            dcounts = (counts[2] - counts[0]).to(torch.float64) / (2.0 * h)
+            slope = float((g_counts * dcounts).sum().cpu())
+        finally:
+            tr.close()
+        return {"t": float(t), "loss": loss, "slope": slope, "curv": (L_p - 2.0 * loss + L_m) / (h * h),
+                "losses": [L_m, loss, L_p], "factors": k.tolist()}
+
+
+def fit_tilt_newton(evaluate, t0, h=1.0, iters=8, tol=0.02, bounds=(0.0, 60.0)):
+    """Safeguarded Newton iteration on the tilt.
+
+    evaluate(t, h) gives the loss, its slope and curvature at t (``TiltAdjoint.evaluate``).
+    The Newton step -slope/curv is clipped to +-h (a step of h downhill where the
+    curvature is not positive).  Once the slope has changed sign between two evaluated
+    tilts, they bracket the minimum: a step that leaves the bracket bisects it instead,
+    and the iteration ends when the bracket is narrower than tol (the slope of a finite
+    sample is jagged on small scales, so a bare Newton iteration can cycle there).  It
+    also ends when a step is shorter than tol.  Returns (tilt, the evaluations in order)."""
+    t = float(t0)
+    lo, hi = -math.inf, math.inf
+    hist = []
+    for _ in range(iters):
+        r = evaluate(t, h)
+        hist.append(r)
+        if r["slope"] > 0.0:
+            hi = min(hi, t)
+        else:
+            lo = max(lo, t)
+        step = -r["slope"] / r["curv"] if r["curv"] > 0.0 else -math.copysign(h, r["slope"])
+        t_new = t + float(np.clip(step, -h, h))
+        if math.isfinite(lo) and math.isfinite(hi):
+            if hi - lo < tol:
+                t_new = 0.5 * (lo + hi)
+                r["step"] = t_new - t
+                t = t_new
+                break
+            if not lo < t_new < hi:
+                t_new = 0.5 * (lo + hi)
+        t_new = float(np.clip(t_new, *bounds))
+        r["step"] = t_new - t
+        t = t_new
+        if abs(r["step"]) < tol:
+            break
+    return t, hist
