@@ -254,18 +254,36 @@ __device__ __forceinline__ bool chi_table_q(const float4* tab, unsigned int* sta
 // cos chi = (1 - T^2)/(1 + T^2), sin chi = 2T/(1 + T^2)
 __device__ __forceinline__ void chi_cos_sin(float q, float& cc, float& sc)
 {
-    const float Tq = expf(fminf(q, 40.0f));
+    const float Tq = __expf(fminf(q, 40.0f));
     const float T2 = Tq * Tq;
-    const float inv = 1.0f / (1.0f + T2);
+    const float inv = __fdividef(1.0f, 1.0f + T2);
     cc = (1.0f - T2) * inv;
     sc = 2.0f * Tq * inv;
 }
+
+// (sin 2 pi u, cos 2 pi u) for u in (0, 1] from the MUFU sine and cosine, whose
+// absolute error bound (about 2^-21.4) holds on [-pi, pi]: 2 pi u = 2 pi (u - 1/2) + pi,
+// and u - 1/2 is exact for u = m 2^-24
+__device__ __forceinline__ void sincos_2pi_fast(float u, float* s, float* c)
+{
+    float ss, cc;
+    __sincosf(6.283185307179586f * (u - 0.5f), &ss, &cc);
+    *s = -ss;
+    *c = -cc;
+}
+
+// -ln u for u in (0, 1] from the MUFU logarithm (absolute error about 2^-21.4 near 1,
+// 3 ulp elsewhere), clamped at 0 where the approximation rounds above zero
+__device__ __forceinline__ float neg_log_fast(float u) { return fmaxf(-__logf(u), 0.0f); }
+
+// sqrt(x) for x >= 0 as x / sqrt(x) from the MUFU reciprocal square root (about 2 ulp); 0 at 0
+__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
 // orthonormal pair perpendicular to unit n (Duff et al., JCGT 6(1), 2017)
 __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& b1, float3& b2)
 {
     float sgn = copysignf(1.0f, nz);
-    float a = -1.0f / (sgn + nz);
+    float a = __fdividef(-1.0f, sgn + nz);
     float b = nx * ny * a;
     b1 = make_float3(1.0f + sgn * nx * nx * a, sgn * b, -sgn * nx);
     b2 = make_float3(b, sgn + ny * ny * a, -ny);
@@ -387,9 +405,13 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
 {
     float t = CUDART_INF_F;
     if (Q.kind == SPUT_PRIM_BOX) {
-        float tx = dx > 0.0f ? (P.box_hi[0] - px) / dx : (dx < 0.0f ? (P.box_lo[0] - px) / dx : CUDART_INF_F);
-        float ty = dy > 0.0f ? (P.box_hi[1] - py) / dy : (dy < 0.0f ? (P.box_lo[1] - py) / dy : CUDART_INF_F);
-        float tz = dz > 0.0f ? (P.box_hi[2] - pz) / dz : (dz < 0.0f ? (P.box_lo[2] - pz) / dz : CUDART_INF_F);
+        // approximate quotients (2 ulp): a hit distance needs no correctly rounded division
+        const float tx = dx > 0.0f ? __fdividef(P.box_hi[0] - px, dx)
+                                   : (dx < 0.0f ? __fdividef(P.box_lo[0] - px, dx) : CUDART_INF_F);
+        const float ty = dy > 0.0f ? __fdividef(P.box_hi[1] - py, dy)
+                                   : (dy < 0.0f ? __fdividef(P.box_lo[1] - py, dy) : CUDART_INF_F);
+        const float tz = dz > 0.0f ? __fdividef(P.box_hi[2] - pz, dz)
+                                   : (dz < 0.0f ? __fdividef(P.box_lo[2] - pz, dz) : CUDART_INF_F);
         t = fmaxf(fminf(tx, fminf(ty, tz)), 0.0f);
     } else if (Q.kind == SPUT_PRIM_CYLINDER) {
         const float wx = px - Q.cx, wy = py - Q.cy, wz = pz - Q.cz;
@@ -404,7 +426,7 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
         if (A > 0.0f && disc >= 0.0f) {
             const float sq = sqrtf(disc);
             const float q = -0.5f * (B + copysignf(sq, B));
-            float r1 = q / A, r2 = q != 0.0f ? Cc / q : r1;
+            float r1 = __fdividef(q, A), r2 = q != 0.0f ? __fdividef(Cc, q) : r1;
             const float tlo = fminf(r1, r2), thi = fmaxf(r1, r2);
             if (tlo > 0.0f && fabsf(fmaf(tlo, da, wa)) <= Q.p1) t = tlo;
             else if (thi > 0.0f && fabsf(fmaf(thi, da, wa)) <= Q.p1) t = thi;
@@ -413,7 +435,7 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
         const float den = dx * Q.nx + dy * Q.ny + dz * Q.nz;
         if (den != 0.0f) {
             const float num = (Q.cx - px) * Q.nx + (Q.cy - py) * Q.ny + (Q.cz - pz) * Q.nz;
-            const float tt = num / den;
+            const float tt = __fdividef(num, den);
             if (tt > 0.0f) {
                 const float qx = fmaf(tt, dx, px) - Q.cx, qy = fmaf(tt, dy, py) - Q.cy, qz = fmaf(tt, dz, pz) - Q.cz;
                 const float a1 = qx * Q.ux + qy * Q.uy + qz * Q.uz;
@@ -494,7 +516,7 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     // diffusion shortcut: exponential steps of mean lambda_D, 1/lambda_D = n sigma_D
     if (kMode == kModeWalk && S.diff) inv_lam = S.ng14 * pr.sigma_D;
     constexpr bool kScoreT = kMode == kModeScoreT;
-    const float ell = S.ng14 > 0.0f ? -logf(rn(w.x)) / inv_lam : CUDART_INF_F;
+    const float ell = S.ng14 > 0.0f ? __fdividef(neg_log_fast(rn(w.x)), inv_lam) : CUDART_INF_F;
     // temperature score: d ln(n_g K(v)/v)/dT = (-1 + G/2)/T with n_g = p/(k_B T), G = d ln K/d ln s
     float aT = 0.0f;
     if (kScoreT) {
@@ -656,11 +678,11 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         float cx = 0.0f, cy = 0.0f, cz = 0.0f;
         if (a < A) {
             const uint4 wn = philox(P.key0, P.key1, o_pid, stream_of(T, P, o_inst), o_k, 1u + (uint32_t)a);
-            const float R0 = sqrtf(-2.0f * logf(rn(wn.x)));
-            const float R1 = sqrtf(-2.0f * logf(rn(wn.z)));
+            const float R0 = sqrt_fast(2.0f * neg_log_fast(rn(wn.x)));
+            const float R1 = sqrt_fast(2.0f * neg_log_fast(rn(wn.z)));
             float s1, c1, s3, c3;
-            sincospif(2.0f * rn(wn.y), &s1, &c1);
-            sincospif(2.0f * rn(wn.w), &s3, &c3);
+            sincos_2pi_fast(rn(wn.y), &s1, &c1);
+            sincos_2pi_fast(rn(wn.w), &s3, &c3);
             const float z1 = R0 * c1, z2 = R0 * s1, z3 = R1 * c3, z4 = R1 * s3;
             // low bytes of words 0, 1, 2 as one more 24-bit uniform
             const uint32_t lowb = ((wn.x & 0xffu) << 24) | ((wn.y & 0xffu) << 16) | ((wn.z & 0xffu) << 8);
@@ -668,16 +690,17 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
             const float ut = rn(lowb) * (o_A + Bm);
             const bool weighted = ut <= Bm;
             const float r32 = z1 * z1 + z2 * z2 + z3 * z3;
-            const float r3 = sqrtf(r32);
-            const float rho = weighted ? sqrtf(r32 + z4 * z4) : r3;
-            const float sc = P.s_gas * (weighted ? (r3 > 0.0f ? rho / r3 : 0.0f) : 1.0f);
+            const float ir3 = r32 > 0.0f ? rsqrtf(r32) : 0.0f;
+            const float r3 = r32 * ir3;
+            const float rho = weighted ? sqrt_fast(r32 + z4 * z4) : r3;
+            const float sc = P.s_gas * (weighted ? rho * ir3 : 1.0f);
             cx = sc * z1;
             cy = sc * z2;
             cz = sc * z3;
             const float gx = o_vx - cx, gy = o_vy - cy, gz = o_vz - cz;
             const float g2 = gx * gx + gy * gy + gz * gz;
             const int op = idx_ok(T.status, o_pair, P.n_pairs) ? o_pair : 0;
-            const float hg = h_of_g(T, pairs[op], sqrtf(g2), g2);
+            const float hg = h_of_g(T, pairs[op], sqrt_fast(g2), g2);
             const float env = fmaf(o_B, rho, o_A);
             // the branch's own uniform, rescaled to (0, 1], times the envelope against h
             acc = (weighted ? ut * env <= Bm * hg : (ut - Bm) * env <= o_A * hg) || a == A - 1;
@@ -720,8 +743,8 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
     const float gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
     const float g2 = gx * gx + gy * gy + gz * gz;
     if (g2 > 0.0f) {
-        const float g = sqrtf(g2);
-        const float ig = 1.0f / g;
+        const float ig = rsqrtf(g2);
+        const float g = g2 * ig;
         const float hx = gx * ig, hy = gy * ig, hz = gz * ig;
         float sc, cc, sp, cp;
         const float ub = rn(w.y);  // impact parameter b = b_max sqrt(ub)
@@ -738,7 +761,7 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
                 sincospif(chi_over_pi_moliere(eps, le, beta, xh_eval(T, le), T.gm), &sc, &cc);
             }
         }
-        sincospif(2.0f * rn(w.z), &sp, &cp);
+        sincos_2pi_fast(rn(w.z), &sp, &cp);
         float3 b1, b2;
         onb(hx, hy, hz, b1, b2);
         const float gpx = g * (cc * hx + sc * (cp * b1.x + sp * b2.x));
@@ -753,9 +776,9 @@ __device__ void scatter(Lane& S, const Params& P, const TableView& T, const DevP
         const float ux = nvx * up, uy = nvy * up, uz = nvz * up;
         const float sp2 = ux * ux + uy * uy + uz * uz;
         if (sp2 > 0.0f) {
-            const float sn = sqrtf(sp2);
-            const float is = 1.0f / sn;
-            S.speed = sn * (1.0f / up);
+            const float is = rsqrtf(sp2);
+            const float sn = sp2 * is;
+            S.speed = up == 1.0f ? sn : sn * 0x1p-60f;
             S.dx = ux * is;
             S.dy = uy * is;
             S.dz = uz * is;
