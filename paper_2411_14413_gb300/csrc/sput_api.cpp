@@ -99,7 +99,6 @@ struct sput_scene {
     std::vector<DevInstance> dinst;
     std::vector<unsigned long long> prefix;
     std::vector<float4> wtab;
-    int n_w_smem = 0;  // leading entries of wtab staged in shared memory (K and M tables)
     std::vector<float4> rt;
     std::vector<std::vector<double>> lt_weights;  // copies of the cathodes' joint launch tables
     std::vector<float> lt;                        // their CDFs (DevCathode::lt_off)
@@ -499,9 +498,8 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
         D.w_inv_h = (float)(1.0 / h_w);
         D.inv_s = (float)(1.0 / S->s_gas);
     }
-    // the d ln K/d ln s tables follow every K, A and B table: only K, A and B are staged in
-    // shared memory; the temperature-score instance reads these from global memory
-    S->n_w_smem = (int)S->wtab.size();
+    // the d ln K/d ln s tables follow every K, A and B table (read by the temperature-score
+    // instance only); the kernel reads all of them through L1
     for (size_t p = 0; p < S->pair_phys.size(); ++p) {
         S->dpairs[p].G_off = (int)S->wtab.size();
         S->wtab.insert(S->wtab.end(), g_tabs[p].begin(), g_tabs[p].end());
@@ -676,7 +674,6 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     p.n_pairs = (int)S->dpairs.size();
     p.n_inst = (int)S->dinst.size();
     p.n_bm = (int)bm.size();
-    p.n_w_total = S->n_w_smem;
     p.n_w_all = (int)S->wtab.size();
     p.n_rt_all = (int)S->rt.size();
     p.n_lt_all = (int)S->lt.size();

@@ -147,7 +147,7 @@ struct Params {
     float cell_lo[3], cell_h, cell_inv_h;
     int cell_n[3];
     int n_prims, n_geoms, n_pairs, n_inst;
-    int n_bm, n_w_total;               // n_w_total: leading w_tab entries (K, M) staged in shared memory
+    int n_bm;
     int n_w_all, n_rt_all, n_lt_all;   // entries of w_tab, rt_tab and lt_tab (bounds of the checked build)
     float bm_lo, bm_inv_h;
     float box_lo[3], box_hi[3];

@@ -97,6 +97,7 @@ struct TableView {
     const float4* w;
     const float4* gm;  // Gauss-Mehler nodes: kGMHalf of the kGMNodes rule, then kGMHalfLo of the kGMNodesLo rule
     const DevPair* pairs;
+    const DevGeom* geoms;
     int n_bm;
     int n_w;           // entries of w (bounds of the checked build)
     float bm_lo, bm_inv_h;
@@ -123,11 +124,17 @@ __device__ __forceinline__ float xh_eval(const TableView& T, float ln_eps)
     return fmaf(t, T.xh[i + 1] - T.xh[i], T.xh[i]);
 }
 
-// K(v), A(v) or B(v) of a pair: cubic pieces in w = ln(1 + v/s), at a given w
+// K(v), A(v) or B(v) of a pair: cubic pieces in w = ln(1 + v/s), at a given w.  The
+// tables are read through L1 from global memory (a few KB per pair, L1-resident), which
+// keeps them out of shared memory so that four blocks fit on an SM.
 __device__ __forceinline__ float wtab_at(const TableView& T, const DevPair& pr, int off, float w)
 {
     if (!idx_ok(T.status, (long long)off + pr.n_w - 1, T.n_w) || !idx_ok(T.status, off, T.n_w)) return 0.0f;
-    return cubic_eval(T.w + off, pr.n_w, w * pr.w_inv_h);
+    const float x = fminf(fmaxf(w * pr.w_inv_h, 0.0f), (float)pr.n_w);
+    const int i = min((int)x, pr.n_w - 1);
+    const float t = x - (float)i;
+    const float4 c = __ldg(T.w + off + i);
+    return fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
 }
 
 __device__ __forceinline__ float wtab_eval(const TableView& T, const DevPair& pr, int off, float v)
@@ -295,10 +302,8 @@ struct Lane {
     float scoreT;  // d ln p(path)/dT (kernel instance with the temperature score only)
     bool diff;     // thermalised: random walk of the diffusion shortcut
     uint32_t pid, inst, k, ncoll;
-    int gbegin, gcount, gsub, target, pair;
-    int gcell;  // the geometry's cell-mask offset (-1: none)
+    int geom, pair;  // geometry index (its record is read from TableView::geoms), gas pair
     float ng14, E_per_v2;
-    unsigned long long ticket;
 };
 
 __device__ __forceinline__ float racetrack_r(const DevCathode& C, const float4* rt_tab, int rt_n, int n_rt_all,
@@ -454,21 +459,15 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
 }
 
 // ------------------------------------------------------------- particle start
-__device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, uint32_t inst, uint32_t pid,
-                               unsigned long long ticket)
+__device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, uint32_t inst, uint32_t pid)
 {
     if (!idx_ok(P.status, inst, P.n_inst)) inst = 0;
     const DevInstance& I = P.inst[inst];
-    const DevGeom G = geoms[idx_ok(P.status, I.geometry, P.n_geoms) ? I.geometry : 0];
+    const int gi = idx_ok(P.status, I.geometry, P.n_geoms) ? I.geometry : 0;
     const DevCathode& C = P.cath[I.cathode];
     S.inst = inst;
     S.pid = pid;
-    S.ticket = ticket;
-    S.gbegin = G.begin;
-    S.gcount = G.count;
-    S.gsub = G.substrate;
-    S.gcell = P.cell_mask ? G.cell_base : -1;
-    S.target = C.target;
+    S.geom = gi;
     S.pair = idx_ok(P.status, I.pair, P.n_pairs) ? I.pair : 0;
     S.ng14 = I.ng14;
     S.E_per_v2 = C.E_per_v2;
@@ -533,12 +532,14 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     // beyond that can be the landing.
     float tb = CUDART_INF_F;
     int hb = -1;
-    const int excl = S.k == 1u ? S.target : -1;
+    // the emitting target is skipped on the first flight (read only then)
+    const DevGeom G = T.geoms[S.geom];
+    const int excl = S.k == 1u ? P.cath[P.inst[S.inst].cathode].target : -1;
     if (!kMasks) {
-        for (int li = 0; li < S.gcount; ++li) {
+        for (int li = 0; li < G.count; ++li) {
             if (li == excl) continue;
-            if (!idx_ok(P.status, S.gbegin + li, P.n_prims)) break;
-            const DevPrim& Q = prims[S.gbegin + li];
+            if (!idx_ok(P.status, G.begin + li, P.n_prims)) break;
+            const DevPrim& Q = prims[G.begin + li];
             if (Q.kind != SPUT_PRIM_BOX) {
                 const float ex = Q.bx - S.px, ey = Q.by - S.py, ez = Q.bz - S.pz;
                 const float reach = fminf(ell, tb) * 1.0001f + Q.br + 1e-3f;
@@ -560,18 +561,18 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
             const int iy = min(max((int)floorf((S.py - P.cell_lo[1]) * P.cell_inv_h), 0), P.cell_n[1] - 1);
             const int iz = min(max((int)floorf((S.pz - P.cell_lo[2]) * P.cell_inv_h), 0), P.cell_n[2] - 1);
             const int c = (iz * P.cell_n[1] + iy) * P.cell_n[0] + ix;
-            near = __ldg(P.cell_mask + S.gcell + 2 * c + (ell <= P.cell_h ? 0 : 1));
+            near = __ldg(P.cell_mask + G.cell_base + 2 * c + (ell <= P.cell_h ? 0 : 1));
         }
-        for (int base = 0; base < S.gcount; base += 32) {
-            const int left = S.gcount - base;
+        for (int base = 0; base < G.count; base += 32) {
+            const int left = G.count - base;
             unsigned mask = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
             if (base < 64) mask &= (unsigned)(near >> base);
             if (excl >= base && excl < base + 32) mask &= ~(1u << (excl - base));
             while (mask) {
                 const int li = base + __ffs(mask) - 1;
                 mask &= mask - 1u;
-                if (!idx_ok(P.status, S.gbegin + li, P.n_prims)) break;
-                const DevPrim& Q = prims[S.gbegin + li];
+                if (!idx_ok(P.status, G.begin + li, P.n_prims)) break;
+                const DevPrim& Q = prims[G.begin + li];
                 if (Q.kind != SPUT_PRIM_BOX) {
                     const float ex = Q.bx - S.px, ey = Q.by - S.py, ez = Q.bz - S.pz;
                     const float reach = fminf(ell, tb) * 1.0001f + Q.br + 1e-3f;
@@ -840,7 +841,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
 
 // ------------------------------------------------------------- kernel
 struct SmemLayout {
-    size_t prims, geoms, pairs, bm, w, prefix, xh, gm, stream, counters, total;
+    size_t prims, geoms, pairs, bm, prefix, xh, gm, stream, pool, counters, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -857,8 +858,6 @@ __host__ __device__ inline SmemLayout smem_layout(const Params& p)
     o = align16(o + sizeof(DevPair) * p.n_pairs);
     L.bm = o;
     o = align16(o + sizeof(float4) * p.n_bm);
-    L.w = o;
-    o = align16(o + sizeof(float4) * p.n_w_total);
     L.prefix = o;
     o = align16(o + sizeof(unsigned long long) * (p.n_inst + 1));
     L.xh = o;
@@ -867,6 +866,8 @@ __host__ __device__ inline SmemLayout smem_layout(const Params& p)
     o = align16(o + sizeof(float4) * (kGMHalf + kGMHalfLo));
     L.stream = o;
     o = align16(o + sizeof(uint32_t) * p.n_inst);
+    L.pool = o;
+    o = align16(o + sizeof(unsigned long long) * 2 * 8);
     L.counters = o;
     o = align16(o + (p.smem_counters ? sizeof(unsigned int) * (size_t)p.n_inst * (p.max_prims + 1) : 0));
     L.total = o;
@@ -883,8 +884,13 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, size_t bytes)
     for (size_t i = (bytes / 16) * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
 }
 
+// Persistent warp pool.  Four blocks of 256 threads per SM (32 warps, 64 registers a
+// thread): the issue-bound loop gains more from the extra warps than it loses to the
+// few spills at 64 registers; the lane state is kept small for it (a geometry index
+// instead of the geometry's fields, the ticket recomputed from (instance, id), the
+// warp's ticket pool in shared memory).
 template <bool kCount64, int kMode, bool kMasks>
-__global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
+__global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout L = smem_layout(P);
@@ -892,18 +898,17 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     DevGeom* s_geoms = reinterpret_cast<DevGeom*>(smem + L.geoms);
     DevPair* s_pairs = reinterpret_cast<DevPair*>(smem + L.pairs);
     float4* s_bm = reinterpret_cast<float4*>(smem + L.bm);
-    float4* s_w = reinterpret_cast<float4*>(smem + L.w);
     unsigned long long* s_prefix = reinterpret_cast<unsigned long long*>(smem + L.prefix);
     float* s_xh = reinterpret_cast<float*>(smem + L.xh);
     float4* s_gm = reinterpret_cast<float4*>(smem + L.gm);
     uint32_t* s_stream = reinterpret_cast<uint32_t*>(smem + L.stream);
+    unsigned long long* s_pool = reinterpret_cast<unsigned long long*>(smem + L.pool);
     unsigned int* s_cnt = reinterpret_cast<unsigned int*>(smem + L.counters);
 
     copy16(s_prims, P.prims, sizeof(DevPrim) * P.n_prims);
     copy16(s_geoms, P.geoms, sizeof(DevGeom) * P.n_geoms);
     copy16(s_pairs, P.pairs, sizeof(DevPair) * P.n_pairs);
     copy16(s_bm, P.bm_tab, sizeof(float4) * P.n_bm);
-    copy16(s_w, P.w_tab, sizeof(float4) * P.n_w_total);
     copy16(s_prefix, P.prefix, sizeof(unsigned long long) * (P.n_inst + 1));
     copy16(s_xh, P.xh_tab, sizeof(float) * (P.n_bm + 1));
     if (threadIdx.x < kGMHalf) s_gm[threadIdx.x] = P.gm[threadIdx.x];
@@ -916,11 +921,12 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     TableView T;
     T.bm = s_bm;
     T.xh = s_xh;
-    T.w = s_w;
+    T.w = P.w_tab;
     T.gm = s_gm;
     T.pairs = s_pairs;
+    T.geoms = s_geoms;
     T.n_bm = P.n_bm;
-    T.n_w = P.n_w_total;
+    T.n_w = P.n_w_all;
     T.bm_lo = P.bm_lo;
     T.bm_inv_h = P.bm_inv_h;
     T.status = P.status;
@@ -933,15 +939,17 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     Lane S;
     S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = S.scoreT = 0.0f;
     S.pid = S.inst = S.k = S.ncoll = 0u;
-    S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
-    S.gcell = -1;
+    S.geom = S.pair = 0;
     S.ng14 = S.E_per_v2 = 0.0f;
-    S.ticket = 0ull;
     bool alive = false;
 
-    uint32_t c_particles = 0, c_landed = 0, c_timed = 0, c_flights = 0, c_coll = 0, c_att = 0;
-    unsigned long long pool_next = 0ull, pool_end = 0ull;
-    bool exhausted = false;
+    // per-lane statistics; particles = landed + timed out, flights = landed + timed out + collided
+    uint32_t c_landed = 0, c_timed = 0, c_coll = 0, c_att = 0;
+    // the warp's ticket pool [next, end) lives in shared memory (warp-uniform, read only
+    // when the warp refills); the pool is exhausted once its end reaches ticket_end
+    unsigned long long* s_wpool = s_pool + 2 * (threadIdx.x >> 5);
+    if (lane == 0) s_wpool[0] = s_wpool[1] = 0ull;
+    __syncwarp();
 
     for (;;) {
         // ---------------------------------------------------- refill (warp-uniform)
@@ -952,6 +960,8 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
         if (need && (__popc(need) >= kRefillMin || need == kFull)) {
             const unsigned n = __popc(need);
             const unsigned rank = __popc(need & lane_lt);
+            unsigned long long pool_next = s_wpool[0], pool_end = s_wpool[1];
+            const bool exhausted = pool_end == P.ticket_end;
             const unsigned long long avail = pool_end - pool_next;
             unsigned long long t = ~0ull;
             if (!alive && rank < avail) t = pool_next + rank;
@@ -966,10 +976,15 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                 unsigned long long nn = base + want < ne ? base + want : ne;
                 pool_next = nn;
                 pool_end = ne;
-                if (base + grab >= P.ticket_end) exhausted = true;
             } else {
                 pool_next += (n < avail ? n : avail);
             }
+            __syncwarp();
+            if (lane == 0) {
+                s_wpool[0] = pool_next;
+                s_wpool[1] = pool_end;
+            }
+            __syncwarp();
             if (t != ~0ull) {
                 // ticket -> (instance, particle id) by binary search over the instance prefix
                 int lo = 0, hi = P.n_inst;
@@ -978,7 +993,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                     if (s_prefix[mid] <= t) lo = mid;
                     else hi = mid;
                 }
-                start_particle(S, P, s_geoms, (uint32_t)lo, (uint32_t)(t - s_prefix[lo]), t);
+                start_particle(S, P, s_geoms, (uint32_t)lo, (uint32_t)(t - s_prefix[lo]));
                 alive = true;
             }
         }
@@ -987,7 +1002,6 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
         // ---------------------------------------------------- one flight (all lanes together)
         StepOut so;
         const int res = flight_step_warp<kMode, kMasks>(alive, S, P, T, s_prims, s_pairs, so);
-        if (alive) ++c_flights;
         c_att += so.attempts;
         if (res == kStepLanded) {
             // ------------------------------------------------ landing tally
@@ -996,8 +1010,9 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
             const float E = S.E_per_v2 * S.speed * S.speed;
             int cell = -1;
             float cosang = 0.0f;
-            if (hb == S.gsub) {
-                const DevPrim& Q = s_prims[S.gbegin + hb];
+            const DevGeom G = s_geoms[S.geom];
+            if (hb == G.substrate) {
+                const DevPrim& Q = s_prims[G.begin + hb];
                 const float dn = S.dx * Q.nx + S.dy * Q.ny + S.dz * Q.nz;
                 if (dn < 0.0f) {
                     const float qx = fmaf(tb, S.dx, S.px) - Q.cx, qy = fmaf(tb, S.dy, S.py) - Q.cy,
@@ -1037,7 +1052,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
             } else if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + hb], 1u);
             else if (P.prim_counts)
                 atomicAdd(reinterpret_cast<unsigned long long*>(P.prim_counts) + (size_t)S.inst * P.max_prims + hb, 1ull);
-            if (P.records && idx_ok(P.status, (long long)(S.ticket - P.ticket_begin),
+            if (P.records && idx_ok(P.status, (long long)(s_prefix[S.inst] + S.pid - P.ticket_begin),
                                     (long long)(P.ticket_end - P.ticket_begin))) {
                 sput_record rec;
                 rec.prim = hb;
@@ -1046,16 +1061,15 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                 rec.cos_angle = cosang;
                 rec.n_collisions = S.ncoll;
                 rec.score = S.score;
-                P.records[S.ticket - P.ticket_begin] = rec;
+                P.records[s_prefix[S.inst] + S.pid - P.ticket_begin] = rec;
             }
             ++c_landed;
-            ++c_particles;
             alive = false;
         } else if (res == kStepTimedOut) {
             if (so.nonfinite) atomicOr(P.status, kStatusNonFinite);
             if (P.smem_counters) atomicAdd(&s_cnt[S.inst * (P.max_prims + 1) + P.max_prims], 1u);
             else if (P.timed_out) atomicAdd(reinterpret_cast<unsigned long long*>(P.timed_out) + S.inst, 1ull);
-            if (P.records && idx_ok(P.status, (long long)(S.ticket - P.ticket_begin),
+            if (P.records && idx_ok(P.status, (long long)(s_prefix[S.inst] + S.pid - P.ticket_begin),
                                     (long long)(P.ticket_end - P.ticket_begin))) {
                 sput_record rec;
                 rec.prim = -1;
@@ -1064,10 +1078,9 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
                 rec.cos_angle = 0.0f;
                 rec.n_collisions = S.ncoll;
                 rec.score = S.score;
-                P.records[S.ticket - P.ticket_begin] = rec;
+                P.records[s_prefix[S.inst] + S.pid - P.ticket_begin] = rec;
             }
             ++c_timed;
-            ++c_particles;
             alive = false;
         } else if (res == kStepCollided) {
             ++c_coll;
@@ -1075,7 +1088,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const Params P)
     }
 
     // ---------------------------------------------------- flush counters
-    unsigned long long v[kNumStats] = {c_particles, c_landed, c_timed, c_flights, c_coll, c_att};
+    unsigned long long v[kNumStats] = {c_landed + c_timed, c_landed, c_timed, c_landed + c_timed + c_coll, c_coll, c_att};
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) {
         unsigned long long x = v[i];
@@ -1113,6 +1126,7 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
     T.w = P.w_tab;
     T.gm = s_gm;
     T.pairs = P.pairs;
+    T.geoms = P.geoms;
     T.n_bm = P.n_bm;
     T.n_w = P.n_w_all;
     T.bm_lo = P.bm_lo;
@@ -1126,12 +1140,11 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         Lane S;
         S.px = S.py = S.pz = S.dx = S.dy = S.dz = S.speed = S.score = S.scoreT = 0.0f;
         S.pid = S.inst = S.k = S.ncoll = 0u;
-        S.gbegin = S.gcount = S.gsub = S.target = S.pair = 0;
+        S.geom = S.pair = 0;
         S.ng14 = S.E_per_v2 = 0.0f;
-        S.ticket = 0ull;
         double* o = valid ? y + (size_t)i * kTraceRows * 10 : nullptr;
         if (valid) {
-            start_particle(S, P, P.geoms, (uint32_t)idx, (uint32_t)x[i], 0ull);
+            start_particle(S, P, P.geoms, (uint32_t)idx, (uint32_t)x[i]);
             for (int r = 0; r < kTraceRows * 10; ++r) o[r] = 0.0;
             for (int r = 1; r < kTraceRows; ++r) o[r * 10 + 7] = -2.0;
             o[0] = S.px; o[1] = S.py; o[2] = S.pz; o[3] = S.dx; o[4] = S.dy; o[5] = S.dz; o[6] = S.speed;
