@@ -607,6 +607,9 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     return kStepCollided;
 }
 
+// correctly rounded 1/d for d = 1..33 (the values __frcp_rn gives), indexed by warp-uniform d
+__constant__ float kRcpSmall[34] = {0.0f, 1.0f / 1.0f, 1.0f / 2.0f, 1.0f / 3.0f, 1.0f / 4.0f, 1.0f / 5.0f, 1.0f / 6.0f, 1.0f / 7.0f, 1.0f / 8.0f, 1.0f / 9.0f, 1.0f / 10.0f, 1.0f / 11.0f, 1.0f / 12.0f, 1.0f / 13.0f, 1.0f / 14.0f, 1.0f / 15.0f, 1.0f / 16.0f, 1.0f / 17.0f, 1.0f / 18.0f, 1.0f / 19.0f, 1.0f / 20.0f, 1.0f / 21.0f, 1.0f / 22.0f, 1.0f / 23.0f, 1.0f / 24.0f, 1.0f / 25.0f, 1.0f / 26.0f, 1.0f / 27.0f, 1.0f / 28.0f, 1.0f / 29.0f, 1.0f / 30.0f, 1.0f / 31.0f, 1.0f / 32.0f, 1.0f / 33.0f};
+
 // position of the n-th (0-based) set bit of mask; mask has more than n set bits
 __device__ __forceinline__ int nth_set_bit(unsigned mask, int n)
 {
@@ -647,19 +650,19 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
     attempts = 0;
     while (pending) {
         // np pending particles share 32 lanes: the first `extra` get m + 1 lanes, the rest m
-        // (small-integer quotients through a correctly rounded reciprocal: 32/np
-        // is exact as np <= 32 divides 32 only as a power of two, and
-        // (l + 1/2)/d stays at least 1/66 away from an integer for l < 32, d <= 33)
+        // (small-integer quotients through a correctly rounded reciprocal from a
+        // table, d = 1..33: 32/np is exact as np <= 32 divides 32 only as a power of
+        // two, and (l + 1/2)/d stays at least 1/66 away from an integer for l < 32)
         const int np = __popc(pending);
-        const int m = (int)(32.0f * __frcp_rn((float)np));
+        const int m = (int)(32.0f * kRcpSmall[np]);
         const int extra = 32 - m * np;
         const int cut = extra * (m + 1);
         int slot, j;
         if (lane < cut) {
-            slot = (int)(((float)lane + 0.5f) * __frcp_rn((float)(m + 1)));
+            slot = (int)(((float)lane + 0.5f) * kRcpSmall[m + 1]);
             j = lane - slot * (m + 1);
         } else {
-            const int r = (int)(((float)(lane - cut) + 0.5f) * __frcp_rn((float)m));
+            const int r = (int)(((float)(lane - cut) + 0.5f) * kRcpSmall[m]);
             slot = extra + r;
             j = lane - cut - r * m;
         }
