@@ -71,9 +71,9 @@ WORKLOAD = WORKLOADS["quaternary"]
 #   surface test (S5): 25 FP32 operations per primitive of the geometry
 #   partner attempt (S7): one Philox block, Box-Muller (2 ln, 2 sqrt, sin, 2 cos
 #     and scaling), relative speed, sigma(g) g from the b_max table, the test
-#   collision (S8): the rejection bound M(v) lookup, relative velocity and its
-#     norm, reduced energy, impact parameter, the deflection from a shared-
-#     memory (ln eps, b) table (1 lg2, 4 loads, bilinear weights), two sincos,
+#   collision (S8): the partner envelope lookup, relative velocity and its
+#     norm, reduced energy, impact parameter, the deflection from an
+#     (ln eps, b) table (1 lg2, 4 loads, bilinear weights), two sincos,
 #     the rotation about g and the CM transform
 #   particle (S1-S3, S6, S9): two Philox blocks, racetrack / Thompson / cosine
 #     inversions and the pose transform, the cell index and tally, the ticket

@@ -291,7 +291,8 @@ const char* sput_last_error(void);
 
 /* Validate the description, build the interaction tables (FP64 on the host:
  * b_max(eps) and the head-on apsis in reduced Moliere units, <sigma g>(v) and
- * the rejection bound M(v) per cathode/gas pair, racetrack guesses) and copy
+ * the partner rejection envelope per cathode/gas pair, the deflection table,
+ * racetrack guesses, the surface test's cell masks) and copy
  * scene and tables to `device`.  On success *out owns device memory until
  * sput_scene_destroy.  Errors: INVALID_ARG, INVALID_SCENE, CUDA, NO_MEMORY. */
 sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scene** out);

@@ -11,7 +11,9 @@
 //   * K(v) = <sigma(g) g> over a Maxwellian gas at T, so that the mean free
 //     path is lambda_m(v) = v / (n_g K(v)) (velocity-dependent lambda_m of the
 //     Eq. for lambda, gas in thermal equilibrium);
-//   * M(v) = max_{g <= v + 6 s} sigma(g) g, the bound of the partner rejection;
+//   * the partner envelope A(v), B(v): the line A + B rho (rho = |V|/s) on the
+//     upper concave hull of H(rho) = max sigma(g) g over the relative speeds a
+//     partner of speed rho s can give, which bounds the rejection's weight;
 //   * first guesses for the racetrack inverse CDF.
 // Everything here is double precision; the device receives FP32 cubic pieces.
 #include "sput_tables.h"

@@ -4,11 +4,13 @@
 // lanes from a warp-private pool of tickets that it takes in chunks from one
 // global counter, so every lane runs exactly one free flight per loop
 // iteration (Sec. "The SIMTRA model": launch, free flight, surface test,
-// binary collision, repeated until the atom lands).  Geometry and the
-// interaction tables are staged in shared memory; the per-collision
-// scattering angle is computed from the classical deflection integral by
-// Gauss-Mehler quadrature in FP32.  Counts are integer atomics (bit-exact,
-// order independent); energy and score sums are FP64 atomics.
+// binary collision, repeated until the atom lands).  The geometry and the small
+// interaction tables are staged in shared memory; the rate tables, the
+// deflection table and the cell masks are read through L1/L2.  The scattering
+// angle comes from a bicubic table of ln tan(chi/2) built from the classical
+// deflection integral, and from Gauss-Mehler quadrature in FP32 outside the
+// table's range.  Counts are integer atomics (bit-exact, order independent);
+// energy and score sums are FP64 atomics.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>

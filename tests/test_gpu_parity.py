@@ -1,8 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances (FP32 device arithmetic against FP64):
-  * sub-steps: scattering angle within 2e-6 rad; b_max, K(v), M(v) within
-    2e-5 relative; launch position within 2e-4 mm, direction within 2e-5,
+  * sub-steps: scattering angle within 2e-6 rad; b_max, K(v) and the partner
+    envelope (A, B) within 2e-5 relative; launch position within 2e-4 mm, direction within 2e-5,
     energy within 2e-5 relative;
   * whole trajectories: at least 99.9 % of particles land on the same
     primitive and substrate cell as the oracle's (same Philox words drive
