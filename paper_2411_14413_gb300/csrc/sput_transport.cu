@@ -30,9 +30,13 @@ constexpr unsigned kFull = 0xffffffffu;
 // kernel instances: the exact transport, with the temperature score, or with the
 // diffusion shortcut for thermalised atoms (the two options exclude each other)
 enum { kModePlain = 0, kModeScoreT = 1, kModeWalk = 2 };
-// dead lanes of a warp that trigger a refill (measured optimum 4-8 on the
-// quaternary workload; 1 = refill every flight)
-constexpr int kRefillMin = 6;
+// A warp refills its dead lanes together, in one pass of the launch code, once
+// kRefillMin of them are dead or once its dead lanes have idled for kRefillIdle
+// lane-steps since the last refill.  The first rule suits short trajectories
+// (lanes die every step or two), the second long ones (a single dead lane would
+// otherwise idle for dozens of steps at 3 Pa).
+constexpr int kRefillMin = 4;
+constexpr int kRefillIdle = 8;
 
 // ----------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
@@ -956,13 +960,16 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     if (lane == 0) s_wpool[0] = s_wpool[1] = 0ull;
     __syncwarp();
 
+    int idle_steps = 0;  // dead-lane flight steps since the warp's last refill (warp-uniform)
     for (;;) {
         // ---------------------------------------------------- refill (warp-uniform)
-        // Dead lanes wait until kRefillMin of them (or the whole warp) can be
+        // Dead lanes wait until several of them (or the whole warp) can be
         // refilled together: one pass of the launch code then serves several
         // lanes, which costs less than the lanes' few idle flights.
         const unsigned need = __ballot_sync(kFull, !alive);
-        if (need && (__popc(need) >= kRefillMin || need == kFull)) {
+        idle_steps += __popc(need);
+        if (need && (__popc(need) >= kRefillMin || idle_steps >= kRefillIdle || need == kFull)) {
+            idle_steps = 0;
             const unsigned n = __popc(need);
             const unsigned rank = __popc(need & lane_lt);
             unsigned long long pool_next = s_wpool[0], pool_end = s_wpool[1];
