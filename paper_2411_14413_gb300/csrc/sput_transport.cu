@@ -30,13 +30,6 @@ constexpr unsigned kFull = 0xffffffffu;
 // kernel instances: the exact transport, with the temperature score, or with the
 // diffusion shortcut for thermalised atoms (the two options exclude each other)
 enum { kModePlain = 0, kModeScoreT = 1, kModeWalk = 2 };
-// A warp refills its dead lanes together, in one pass of the launch code, once
-// kRefillMin of them are dead or once its dead lanes have idled for kRefillIdle
-// lane-steps since the last refill.  The first rule suits short trajectories
-// (lanes die every step or two), the second long ones (a single dead lane would
-// otherwise idle for dozens of steps at 3 Pa).
-constexpr int kRefillMin = 4;
-constexpr int kRefillIdle = 8;
 
 // ----------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
@@ -465,29 +458,57 @@ __device__ __forceinline__ float hit_prim(const DevPrim& Q, const Params& P, flo
 }
 
 // ------------------------------------------------------------- particle start
-__device__ void start_particle(Lane& S, const Params& P, const DevGeom* geoms, uint32_t inst, uint32_t pid)
+// A prepared launch: position, direction and speed of particle (inst, pid).
+struct Launch {
+    float px, py, pz, dx, dy, dz, speed;
+    uint32_t inst, pid;
+};
+constexpr int kLaunchWords = 9;  // 32-bit words of a Launch in a warp's shared-memory queue
+
+__device__ Launch prepare_launch(const Params& P, uint32_t inst, uint32_t pid)
 {
     if (!idx_ok(P.status, inst, P.n_inst)) inst = 0;
+    const DevCathode& C = P.cath[P.inst[inst].cathode];
+    Launch L;
+    float E;
+    launch_state(P, P.rt_tab, inst, pid, L.px, L.py, L.pz, L.dx, L.dy, L.dz, E);
+    L.speed = C.v_per_sqrtE * sqrtf(E);
+    L.inst = inst;
+    L.pid = pid;
+    return L;
+}
+
+// The lane takes up the prepared particle.
+__device__ void start_from(Lane& S, const Params& P, const Launch& L)
+{
+    const uint32_t inst = L.inst;
     const DevInstance& I = P.inst[inst];
-    const int gi = idx_ok(P.status, I.geometry, P.n_geoms) ? I.geometry : 0;
-    const DevCathode& C = P.cath[I.cathode];
     S.inst = inst;
-    S.pid = pid;
-    S.geom = gi;
+    S.pid = L.pid;
+    S.geom = idx_ok(P.status, I.geometry, P.n_geoms) ? I.geometry : 0;
     S.pair = idx_ok(P.status, I.pair, P.n_pairs) ? I.pair : 0;
     S.ng14 = I.ng14;
-    S.E_per_v2 = C.E_per_v2;
-    float E;
-    launch_state(P, P.rt_tab, inst, pid, S.px, S.py, S.pz, S.dx, S.dy, S.dz, E);
-    S.speed = C.v_per_sqrtE * sqrtf(E);
+    S.E_per_v2 = P.cath[I.cathode].E_per_v2;
+    S.px = L.px;
+    S.py = L.py;
+    S.pz = L.pz;
+    S.dx = L.dx;
+    S.dy = L.dy;
+    S.dz = L.dz;
+    S.speed = L.speed;
     // failure-path test aid (SPUT_RUN_INJECT_NONFINITE): a non-finite state that the
     // flight step retires with the non-finite status bit
-    if (P.inject_nonfinite && pid == 0u) S.speed = CUDART_NAN_F;
+    if (P.inject_nonfinite && L.pid == 0u) S.speed = CUDART_NAN_F;
     S.k = 0u;
     S.ncoll = 0u;
     S.score = 0.0f;
     S.scoreT = 0.0f;
     S.diff = false;
+}
+
+__device__ void start_particle(Lane& S, const Params& P, uint32_t inst, uint32_t pid)
+{
+    start_from(S, P, prepare_launch(P, inst, pid));
 }
 
 // ------------------------------------------------------------- one flight
@@ -850,7 +871,7 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
 
 // ------------------------------------------------------------- kernel
 struct SmemLayout {
-    size_t prims, geoms, pairs, bm, prefix, xh, gm, stream, pool, counters, total;
+    size_t prims, geoms, pairs, bm, prefix, xh, gm, stream, pool, queue, counters, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -876,7 +897,9 @@ __host__ __device__ inline SmemLayout smem_layout(const Params& p)
     L.stream = o;
     o = align16(o + sizeof(uint32_t) * p.n_inst);
     L.pool = o;
-    o = align16(o + sizeof(unsigned long long) * 2 * 8);
+    o = align16(o + sizeof(unsigned long long) * 4 * 8);
+    L.queue = o;
+    o = align16(o + sizeof(uint32_t) * kLaunchWords * 32 * 8);
     L.counters = o;
     o = align16(o + (p.smem_counters ? sizeof(unsigned int) * (size_t)p.n_inst * (p.max_prims + 1) : 0));
     L.total = o;
@@ -912,6 +935,7 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     float4* s_gm = reinterpret_cast<float4*>(smem + L.gm);
     uint32_t* s_stream = reinterpret_cast<uint32_t*>(smem + L.stream);
     unsigned long long* s_pool = reinterpret_cast<unsigned long long*>(smem + L.pool);
+    uint32_t* s_queue = reinterpret_cast<uint32_t*>(smem + L.queue);
     unsigned int* s_cnt = reinterpret_cast<unsigned int*>(smem + L.counters);
 
     copy16(s_prims, P.prims, sizeof(DevPrim) * P.n_prims);
@@ -956,58 +980,93 @@ __global__ void __launch_bounds__(256, 4) transport_kernel(const Params P)
     uint32_t c_landed = 0, c_timed = 0, c_coll = 0, c_att = 0;
     // the warp's ticket pool [next, end) lives in shared memory (warp-uniform, read only
     // when the warp refills); the pool is exhausted once its end reaches ticket_end
-    unsigned long long* s_wpool = s_pool + 2 * (threadIdx.x >> 5);
-    if (lane == 0) s_wpool[0] = s_wpool[1] = 0ull;
+    // and its queue of prepared launches: s_wpool[2] entries of kLaunchWords words
+    unsigned long long* s_wpool = s_pool + 4 * (threadIdx.x >> 5);
+    uint32_t* s_wqueue = s_queue + kLaunchWords * 32 * (threadIdx.x >> 5);
+    if (lane == 0) s_wpool[0] = s_wpool[1] = s_wpool[2] = 0ull;
     __syncwarp();
 
-    int idle_steps = 0;  // dead-lane flight steps since the warp's last refill (warp-uniform)
     for (;;) {
         // ---------------------------------------------------- refill (warp-uniform)
-        // Dead lanes wait until several of them (or the whole warp) can be
-        // refilled together: one pass of the launch code then serves several
-        // lanes, which costs less than the lanes' few idle flights.
+        // Dead lanes take prepared launches from the warp's queue at once.  When the
+        // queue runs short, the whole warp prepares the next launches together, one
+        // per lane, so the launch code runs with every lane busy instead of once for
+        // a few dead lanes while the others wait.
         const unsigned need = __ballot_sync(kFull, !alive);
-        idle_steps += __popc(need);
-        if (need && (__popc(need) >= kRefillMin || idle_steps >= kRefillIdle || need == kFull)) {
-            idle_steps = 0;
+        if (need) {
             const unsigned n = __popc(need);
             const unsigned rank = __popc(need & lane_lt);
-            unsigned long long pool_next = s_wpool[0], pool_end = s_wpool[1];
-            const bool exhausted = pool_end == P.ticket_end;
-            const unsigned long long avail = pool_end - pool_next;
-            unsigned long long t = ~0ull;
-            if (!alive && rank < avail) t = pool_next + rank;
-            if (n > avail && !exhausted) {
-                const unsigned long long want = n - avail;
-                const unsigned long long grab = want > (unsigned long long)P.chunk ? want : (unsigned long long)P.chunk;
-                unsigned long long base = 0ull;
-                if (lane == 0) base = atomicAdd(P.ticket_counter, grab);
-                base = __shfl_sync(kFull, base, 0) + P.ticket_begin;
-                if (!alive && rank >= avail && base + (rank - avail) < P.ticket_end) t = base + (rank - avail);
-                unsigned long long ne = base + grab < P.ticket_end ? base + grab : P.ticket_end;
-                unsigned long long nn = base + want < ne ? base + want : ne;
-                pool_next = nn;
-                pool_end = ne;
-            } else {
-                pool_next += (n < avail ? n : avail);
-            }
-            __syncwarp();
-            if (lane == 0) {
-                s_wpool[0] = pool_next;
-                s_wpool[1] = pool_end;
-            }
-            __syncwarp();
-            if (t != ~0ull) {
-                // ticket -> (instance, particle id) by binary search over the instance prefix
-                int lo = 0, hi = P.n_inst;
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) >> 1;
-                    if (s_prefix[mid] <= t) lo = mid;
-                    else hi = mid;
+            unsigned qn = (unsigned)s_wpool[2];  // prepared launches in the queue (warp-uniform)
+            if (qn < n) {
+                // the whole warp prepares launches for up to 32 - qn new tickets, one per lane,
+                // so that the launch code runs with every lane busy
+                const unsigned want = 32u - qn;
+                unsigned long long pool_next = s_wpool[0], pool_end = s_wpool[1];
+                const bool exhausted = pool_end == P.ticket_end;
+                const unsigned long long avail = pool_end - pool_next;
+                unsigned long long t = ~0ull;
+                if ((unsigned)lane < want && lane < avail) t = pool_next + lane;
+                if (want > avail && !exhausted) {
+                    const unsigned long long more = want - avail;
+                    const unsigned long long grab = more > (unsigned long long)P.chunk ? more : (unsigned long long)P.chunk;
+                    unsigned long long base = 0ull;
+                    if (lane == 0) base = atomicAdd(P.ticket_counter, grab);
+                    base = __shfl_sync(kFull, base, 0) + P.ticket_begin;
+                    if ((unsigned)lane < want && lane >= avail && base + (lane - avail) < P.ticket_end)
+                        t = base + (lane - avail);
+                    const unsigned long long ne = base + grab < P.ticket_end ? base + grab : P.ticket_end;
+                    const unsigned long long nn = base + more < ne ? base + more : ne;
+                    pool_next = nn;
+                    pool_end = ne;
+                } else {
+                    pool_next += (want < avail ? want : avail);
                 }
-                start_particle(S, P, s_geoms, (uint32_t)lo, (uint32_t)(t - s_prefix[lo]));
+                if (t != ~0ull) {
+                    // ticket -> (instance, particle id) by binary search over the instance prefix
+                    int lo = 0, hi = P.n_inst;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_prefix[mid] <= t) lo = mid;
+                        else hi = mid;
+                    }
+                    const Launch Ln = prepare_launch(P, (uint32_t)lo, (uint32_t)(t - s_prefix[lo]));
+                    uint32_t* e = s_wqueue + kLaunchWords * (qn + lane);
+                    e[0] = __float_as_uint(Ln.px);
+                    e[1] = __float_as_uint(Ln.py);
+                    e[2] = __float_as_uint(Ln.pz);
+                    e[3] = __float_as_uint(Ln.dx);
+                    e[4] = __float_as_uint(Ln.dy);
+                    e[5] = __float_as_uint(Ln.dz);
+                    e[6] = __float_as_uint(Ln.speed);
+                    e[7] = Ln.inst;
+                    e[8] = Ln.pid;
+                }
+                qn += __popc(__ballot_sync(kFull, t != ~0ull));  // the lanes with tickets are a prefix
+                __syncwarp();
+                if (lane == 0) {
+                    s_wpool[0] = pool_next;
+                    s_wpool[1] = pool_end;
+                }
+            }
+            // the dead lanes take launches from the top of the queue
+            if (!alive && rank < qn) {
+                const uint32_t* e = s_wqueue + kLaunchWords * (qn - 1u - rank);
+                Launch Ln;
+                Ln.px = __uint_as_float(e[0]);
+                Ln.py = __uint_as_float(e[1]);
+                Ln.pz = __uint_as_float(e[2]);
+                Ln.dx = __uint_as_float(e[3]);
+                Ln.dy = __uint_as_float(e[4]);
+                Ln.dz = __uint_as_float(e[5]);
+                Ln.speed = __uint_as_float(e[6]);
+                Ln.inst = e[7];
+                Ln.pid = e[8];
+                start_from(S, P, Ln);
                 alive = true;
             }
+            __syncwarp();
+            if (lane == 0) s_wpool[2] = qn - (n < qn ? n : qn);
+            __syncwarp();
         }
         if (!__any_sync(kFull, alive)) break;
 
@@ -1156,7 +1215,7 @@ __global__ void probe_kernel(const Params P, int what, int idx, int n, const dou
         S.ng14 = S.E_per_v2 = 0.0f;
         double* o = valid ? y + (size_t)i * kTraceRows * 10 : nullptr;
         if (valid) {
-            start_particle(S, P, P.geoms, (uint32_t)idx, (uint32_t)x[i]);
+            start_particle(S, P, (uint32_t)idx, (uint32_t)x[i]);
             for (int r = 0; r < kTraceRows * 10; ++r) o[r] = 0.0;
             for (int r = 1; r < kTraceRows; ++r) o[r * 10 + 7] = -2.0;
             o[0] = S.px; o[1] = S.py; o[2] = S.pz; o[3] = S.dx; o[4] = S.dy; o[5] = S.dz; o[6] = S.speed;
