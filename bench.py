@@ -313,6 +313,10 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"{r['particles']} particles ({n_cpu} per instance) of the workload, "
                          f"{r['seconds']:.1f} s wall on {r['cores']} threads",
                "landed_per_s": r["landed"] / r["seconds"]}
+        # the same oracle on one thread, on a quarter of the sample
+        r1 = cpu_oracle_rate(max(1, n_cpu // 4), n_threads=1, workload=args.workload)
+        cpu["single_thread"] = {"value": r1["collisions"] / r1["seconds"], "unit": UNIT, "cores": 1,
+                                "sample": f"{r1['particles']} particles, {r1['seconds']:.1f} s wall on 1 thread"}
         log("cpu baseline:", cpu)
 
     sc = headline_scene(workloads, args)
@@ -440,7 +444,7 @@ def run_ours(args, rank, world, local_rank):
                        "step_ms": step_ms},
     }
     if cpu is not None:
-        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "single_thread")}
     if world == 1 and not args.no_extras:
         line["sub"] = run_extras(args, torch, pkg, api, workloads, dev, peaks)
     print(json.dumps(line), flush=True)
