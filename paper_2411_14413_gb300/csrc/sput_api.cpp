@@ -212,7 +212,7 @@ sput_status validate(const sput_scene_desc* d)
 
 sput_status validate_instances(const sput_scene* S, const sput_instance* inst, int n, const sput_cathode* cath,
                                int n_cath, const sput_geometry* geoms, int n_geoms, const sput_primitive* prims,
-                               int count_type)
+                               int count_type, double gas_mass)
 {
     unsigned long long total = 0;
     for (int i = 0; i < n; ++i) {
@@ -225,6 +225,9 @@ sput_status validate_instances(const sput_scene* S, const sput_instance* inst, i
             return fail(SPUT_ERR_INVALID_SCENE, "cathode target must be a DISC of the instance geometry");
         if (!(I.pressure >= 0.0) || !std::isfinite(I.pressure) || !(I.E_i > 0.0) || !(I.k > 0.0))
             return fail(SPUT_ERR_INVALID_SCENE, "instance needs pressure >= 0, E_i > 0, k > 0");
+        // the Thompson distribution needs a positive cut-off (a launch table brings its own range)
+        if (!C.launch_table && !(thompson_emax(I.k, gas_mass, C.mass, I.E_i, C.U_s) > 0.0))
+            return fail(SPUT_ERR_INVALID_SCENE, "E_max = k Lambda E_i - U_s must be > 0");
         if (I.n_particles >= (1ull << 32)) return fail(SPUT_ERR_INVALID_SCENE, "more than 2^32-1 particles in one instance");
         total += I.n_particles;
     }
@@ -369,7 +372,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
     sput_status st = validate(desc);
     if (st != SPUT_OK) return st;
     st = validate_instances(nullptr, desc->instances, desc->n_instances, desc->cathodes, desc->n_cathodes, desc->geoms,
-                            desc->n_geoms, desc->prims, desc->grid.count_type);
+                            desc->n_geoms, desc->prims, desc->grid.count_type, desc->chamber.gas_mass);
     if (st != SPUT_OK) return st;
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
@@ -737,7 +740,8 @@ sput_status sput_instances_set(sput_scene* S, const sput_instance* instances, in
         if (instances[i].geometry != S->instances[i].geometry || instances[i].cathode != S->instances[i].cathode)
             return fail(SPUT_ERR_INVALID_ARG, "instance geometry and cathode must not change");
     sput_status st = validate_instances(S, instances, n, S->cathodes.data(), (int)S->cathodes.size(), S->geoms.data(),
-                                        (int)S->geoms.size(), S->prims.data(), S->grid.count_type);
+                                        (int)S->geoms.size(), S->prims.data(), S->grid.count_type,
+                                        S->chamber.gas_mass);
     if (st != SPUT_OK) return st;
     std::vector<sput_instance> old = S->instances;
     S->instances.assign(instances, instances + n);

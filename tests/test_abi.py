@@ -108,6 +108,13 @@ def _create(scene):
     (lambda s: s.cathodes[0].__setitem__("launch_table", {"weights": np.full((4, 4), np.nan), "E_hi": 100.0}), 2),
     (lambda s: s.physics.__setitem__("thermal_switch_eV", -1.0), 2),
     (lambda s: s.physics.update({"thermal_switch_eV": 0.1, "gas_motion": "stationary"}), 2),
+    # degenerate conditions of the method: no Thompson support (k Lambda E_i <= U_s), a
+    # negative or undefined pressure, no head-on factor, a gas at or below 0 K
+    (lambda s: s.instances[0].__setitem__("E_i", 5.0), 2),
+    (lambda s: s.instances[0].__setitem__("pressure", -0.1), 2),
+    (lambda s: s.instances[0].__setitem__("pressure", float("nan")), 2),
+    (lambda s: s.instances[0].__setitem__("k", 0.0), 2),
+    (lambda s: setattr(s, "T", 0.0), 2),
 ])
 def test_host_validation_rejects_bad_scenes(lib, mutate, expect):
     """Invalid descriptions fail in host validation, before any CUDA call."""
