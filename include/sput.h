@@ -294,7 +294,12 @@ const char* sput_last_error(void);
  * the partner rejection envelope per cathode/gas pair, the deflection table,
  * racetrack guesses, the surface test's cell masks) and copy
  * scene and tables to `device`.  On success *out owns device memory until
- * sput_scene_destroy.  Errors: INVALID_ARG, INVALID_SCENE, CUDA, NO_MEMORY. */
+ * sput_scene_destroy.  Errors: INVALID_ARG, INVALID_SCENE (found on the host
+ * before any CUDA call, e.g. an instance whose Thompson cut-off
+ * E_max = k Lambda E_i - U_s is not positive), CUDA, NO_MEMORY, and UNSUPPORTED
+ * when the primitives and small tables a block stages do not fit its shared
+ * memory (about 2800 primitives).  Geometries of more than 64 primitives run the
+ * surface test without cell masks. */
 sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scene** out);
 
 /* Replace the instance table (pressures, ion energies, k, particle counts).
