@@ -89,11 +89,11 @@ WORK_MODEL = {"philox_block": PHILOX_BLOCK_OPS, "flight": OPS_PER_FLIGHT, "prim_
 # kernel (ncu smsp__thread_inst_executed.sum / collisions of one launch, small
 # case of the workload); the issue share is reported beside the algorithmic
 # fraction.  None = no capture of the current build.
-EXEC_LANE_INSTR_PER_COLLISION = {"quaternary": 1891.0, "large": 2755.0}
+EXEC_LANE_INSTR_PER_COLLISION = {"quaternary": 1828.0, "large": 2686.0}
 # DRAM bytes (read + write) of one launch of the quaternary workload, from the
-# one-pass capture of the current kernel (mean of 5 launches: 3.89 MB read,
-# 0.84 MB written); None whenever the kernel changed after the capture.
-TRAFFIC_PER_LAUNCH = 4.73e6
+# one-pass capture of the current kernel (mean of 5 launches: 4.09 MB read,
+# 0.23 MB written); None whenever the kernel changed after the capture.
+TRAFFIC_PER_LAUNCH = 4.31e6
 
 
 def log(*a):

@@ -72,6 +72,18 @@ double thompson_emax(double k, double Mi, double Mt, double Ei, double Us)
     return k * 4.0 * Mi * Mt / ((Mi + Mt) * (Mi + Mt)) * Ei - Us;
 }
 
+// Philox4x32-10 key of a run (the seed's two 32-bit halves) and its key schedule: round r
+// uses (key0 + r W0, key1 + r W1) with the published Weyl increments, modulo 2^32.
+void set_philox_keys(sput::Params& p, uint64_t seed)
+{
+    p.key0 = (uint32_t)seed;
+    p.key1 = (uint32_t)(seed >> 32);
+    for (uint32_t r = 0; r < 10; ++r) {
+        p.rk0[r] = p.key0 + r * 0x9E3779B9u;
+        p.rk1[r] = p.key1 + r * 0xBB67AE85u;
+    }
+}
+
 }  // namespace
 
 void sput::set_last_error(const char* msg) { g_last_error = msg; }
@@ -652,6 +664,7 @@ sput_status sput_scene_create(const sput_scene_desc* desc, int device, sput_scen
 
     Params& p = S->base;
     std::memset(&p, 0, sizeof p);
+    set_philox_keys(p, 0);  // the probe kernel's draws use key 0
     p.prims = reinterpret_cast<const DevPrim*>(S->d_blob + S->off_prims);
     p.geoms = reinterpret_cast<const DevGeom*>(S->d_blob + S->off_geoms);
     p.cath = reinterpret_cast<const DevCathode*>(S->d_blob + S->off_cath);
@@ -842,8 +855,7 @@ sput_status run_impl(sput_scene* S, const sput_run_opts* opts, cudaStream_t stre
     p.hist_E = reinterpret_cast<long long*>(T->hist_E);
     p.hist_A = reinterpret_cast<long long*>(T->hist_A);
     p.records = T->records;
-    p.key0 = (uint32_t)opts->seed;
-    p.key1 = (uint32_t)(opts->seed >> 32);
+    set_philox_keys(p, opts->seed);
     p.ticket_begin = tb;
     p.ticket_end = te;
     p.chunk = chunk;
@@ -1205,8 +1217,7 @@ sput_status sput_graph_launch(sput_graph* G, uint64_t seed, void* stream)
 {
     if (!G) return fail(SPUT_ERR_INVALID_ARG, "graph is NULL");
     DeviceGuard guard(G->S->device);
-    G->params.key0 = (uint32_t)seed;
-    G->params.key1 = (uint32_t)(seed >> 32);
+    set_philox_keys(G->params, seed);
     G->args[0] = &G->params;
     cudaKernelNodeParams kp = G->kp;
     kp.kernelParams = G->args;

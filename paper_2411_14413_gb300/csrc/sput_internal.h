@@ -175,6 +175,9 @@ struct Params {
     sput_record* records;
     // run
     uint32_t key0, key1;
+    // the Philox key schedule of this seed, (key0 + r W0, key1 + r W1) for rounds r = 0..9,
+    // set by set_philox_keys (the kernel reads it from the parameter bank)
+    uint32_t rk0[10], rk1[10];
     unsigned long long ticket_begin, ticket_end;
     int chunk;
     int smem_counters;                 // prim/timed-out counters privatised in shared memory

@@ -33,23 +33,20 @@ enum { kModePlain = 0, kModeScoreT = 1, kModeWalk = 2 };
 
 // ----------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
-// multiplies with the published multipliers and Weyl key increments.  Kept
-// out of line: one copy instead of one per call site keeps the hot loop small
-// enough for the instruction cache.
-__device__ __noinline__ uint4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
-                                        uint32_t c3)
+// multiplies with the published multipliers, keyed by the seed's key schedule
+// (Weyl increments), which the host writes into the kernel parameters
+// (set_philox_keys): each round's key is an operand from the parameter bank, not
+// an addition.  Inlined: an out-of-line call made the caller save registers
+// around it at 64 registers a thread.
+__device__ __forceinline__ uint4 philox(const Params& P, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
         const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
         const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        c0 = hi1 ^ c1 ^ k0;
+        c0 = hi1 ^ c1 ^ P.rk0[r];
         c1 = lo1;
-        c2 = hi0 ^ c3 ^ k1;
+        c2 = hi0 ^ c3 ^ P.rk1[r];
         c3 = lo0;
     }
     return make_uint4(c0, c1, c2, c3);
@@ -380,8 +377,8 @@ __device__ void launch_state(const Params& P, const float4* rt_tab, uint32_t ins
 {
     const DevInstance& I = P.inst[inst];
     const DevCathode& C = P.cath[I.cathode];
-    const uint4 w0 = philox(P.key0, P.key1, pid, I.stream, 0u, 0u);
-    const uint4 w1 = philox(P.key0, P.key1, pid, I.stream, 0u, 1u);
+    const uint4 w0 = philox(P, pid, I.stream, 0u, 0u);
+    const uint4 w1 = philox(P, pid, I.stream, 0u, 1u);
     const float r = racetrack_r(C, rt_tab, P.rt_n, P.n_rt_all, P.status, rn(w0.x));
     float sa, ca;
     sincospif(2.0f * rn(w0.y), &sa, &ca);
@@ -538,7 +535,7 @@ __device__ int flight_move(Lane& S, const Params& P, const TableView& T, const D
     out.attempts = 0;
     out.nonfinite = 0;
     out.prim = -1;
-    w = philox(P.key0, P.key1, S.pid, stream_of(T, P, S.inst), S.k, 0u);
+    w = philox(P, S.pid, stream_of(T, P, S.inst), S.k, 0u);
     const DevPair pr = pairs[S.pair];
     // inverse mean free path n_g <sigma g>/v (thermal) or n_g sigma(v) (gas at rest)
     const float Kv = wtab_eval(T, pr, pr.K_off, S.speed);
@@ -712,7 +709,7 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         bool acc = false;
         float cx = 0.0f, cy = 0.0f, cz = 0.0f;
         if (a < A) {
-            const uint4 wn = philox(P.key0, P.key1, o_pid, stream_of(T, P, o_inst), o_k, 1u + (uint32_t)a);
+            const uint4 wn = philox(P, o_pid, stream_of(T, P, o_inst), o_k, 1u + (uint32_t)a);
             const float R0 = sqrt_fast(2.0f * neg_log_fast(rn(wn.x)));
             const float R1 = sqrt_fast(2.0f * neg_log_fast(rn(wn.z)));
             float s1, c1, s3, c3;
