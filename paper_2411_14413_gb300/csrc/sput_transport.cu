@@ -666,7 +666,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned mask, int n)
 // sequential rejection loop's result while every lane stays busy.  Must be
 // called by all 32 lanes together.
 __device__ void partner_sample_warp(bool need, const Params& P, const TableView& T, const DevPair* pairs,
-                                    uint32_t pid, uint32_t inst, uint32_t k, int pair, float vx, float vy, float vz,
+                                    uint32_t pid, uint32_t strm, uint32_t k, int pair, float vx, float vy, float vz,
                                     float EA, float EB, float& Vx, float& Vy, float& Vz, int& attempts)
 {
     const int lane = threadIdx.x & 31;
@@ -696,7 +696,7 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         }
         const int owner = nth_set_bit(pending, slot);
         const uint32_t o_pid = __shfl_sync(kFull, pid, owner);
-        const uint32_t o_inst = __shfl_sync(kFull, inst, owner);
+        const uint32_t o_strm = __shfl_sync(kFull, strm, owner);
         const uint32_t o_k = __shfl_sync(kFull, k, owner);
         const int o_pair = __shfl_sync(kFull, pair, owner);
         const float o_vx = __shfl_sync(kFull, vx, owner);
@@ -709,7 +709,7 @@ __device__ void partner_sample_warp(bool need, const Params& P, const TableView&
         bool acc = false;
         float cx = 0.0f, cy = 0.0f, cz = 0.0f;
         if (a < A) {
-            const uint4 wn = philox(P, o_pid, stream_of(T, P, o_inst), o_k, 1u + (uint32_t)a);
+            const uint4 wn = philox(P, o_pid, o_strm, o_k, 1u + (uint32_t)a);
             const float R0 = sqrt_fast(2.0f * neg_log_fast(rn(wn.x)));
             const float R1 = sqrt_fast(2.0f * neg_log_fast(rn(wn.z)));
             float s1, c1, s3, c3;
@@ -847,8 +847,9 @@ __device__ int flight_step_warp(bool active, Lane& S, const Params& P, const Tab
             EA = wtab_at(T, pr, pr.A_off, w);
             EB = wtab_at(T, pr, pr.B_off, w);
         }
-        partner_sample_warp(coll, P, T, pairs, S.pid, S.inst, S.k, S.pair, vx, vy, vz, EA, EB, Vx, Vy, Vz,
-                            out.attempts);
+        // the owner's Philox stream word travels with it (one shuffle instead of a lookup per attempt)
+        partner_sample_warp(coll, P, T, pairs, S.pid, stream_of(T, P, S.inst), S.k, S.pair, vx, vy, vz, EA, EB, Vx,
+                            Vy, Vz, out.attempts);
         // partner density f_T(V) sigma(g) g / K(v): d ln/dT = (|V|^2/(2 s^2) - 3/2 - G/2)/T
         if (kScoreT && coll)
             S.scoreT += (0.5f * (Vx * Vx + Vy * Vy + Vz * Vz) * P.inv_s2 - 1.5f - 0.5f * out.Gv) * P.inv_T;
